@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Throughput of the tensor butterfly apply u = K f (Alg. 2) on GB300.
+
+One step = one full apply (source leaves, source transfers, mid-level core,
+target transfers, target leaves) of the workload's operator to its batch of
+right-hand sides, inputs resident in HBM.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Multi-GPU (torchrun): each rank holds its own copy of the operator and applies
+its own batch of right-hand sides (replicas, weak scaling); the timed region
+is bracketed by barriers and the max over ranks is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "TB apply Gpts·RHS/s & % roofline, mixed/batched vs FP64 plain at stated rel err"
+UNIT = "Gpts*RHS/s"
+DEFAULT_WORKLOAD = "helmholtz3d_n256"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(W.WORKLOADS))
+    p.add_argument("--precision", type=int, default=None, help="0 c128, 1 c64, 2 split-bf16")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--err-samples", type=int, default=16)
+    p.add_argument("--profile-only", action="store_true", help="eager applies only (for ncu)")
+    p.add_argument("--n", type=int, default=None, help="points per axis of a reduced-size copy (profiling)")
+    return p.parse_args()
+
+
+def workload(args):
+    w = W.WORKLOADS[args.workload]
+    return W.small(args.workload, args.n, nv=w.nv) if args.n else w
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            j = json.load(fh)
+        return {"hbm_gbs": j["hbm_gbs"], "bf16_tflops": j["bf16_tflops"],
+                "bf16_tflops_sustained": j.get("bf16_tflops_sustained"), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def cpu_baseline(w, f_np, budget_s=15.0, seed=4096):
+    """The oracle direct sum, as it stands, on a bounded sample of output points."""
+    import oracle
+    oracle.build()
+    xs, ys = W.grids(w)
+    probe = W.sample_targets(w, 2, seed=seed + 1)
+    t0 = time.perf_counter()
+    oracle.apply(w.kind, w.params, xs, ys, f_np, probe)
+    per = max((time.perf_counter() - t0) / 2, 1e-6)
+    # the direct sum parallelizes over targets: keep at least one target per thread
+    count = int(max(oracle.threads(), min(4096, budget_s / per * oracle.threads())))
+    rows = W.sample_targets(w, count, seed=seed)
+    t0 = time.perf_counter()
+    oracle.apply(w.kind, w.params, xs, ys, f_np, rows)
+    t = time.perf_counter() - t0
+    nv = f_np.shape[-1]
+    return {"value": count * nv / t / 1e9, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{count} sampled output points x {nv} RHS of the direct FP64 sum ({t:.1f} s)"}
+
+
+def reference_arm(args, ws, rank):
+    w = workload(args)
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    f = W.rhs(w).numpy()
+    xs, ys = W.grids(w)
+    probe = W.sample_targets(w, 2, seed=7)
+    t0 = time.perf_counter()
+    oracle.apply(w.kind, w.params, xs, ys, f, probe)
+    per = max((time.perf_counter() - t0) / 2, 1e-6)
+    total = max(args.steps + args.warmup, 1)
+    count = int(max(oracle.threads(), min(4096, 120.0 / total / per * oracle.threads())))
+    times = []
+    for s in range(args.warmup + args.steps):
+        rows = W.sample_targets(w, count, seed=1000 + s)
+        t0 = time.perf_counter()
+        oracle.apply(w.kind, w.params, xs, ys, f, rows)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    val = count * w.nv / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "n": w.n, "d": w.d, "nv": w.nv, "tol": w.tol},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"{count} sampled output points x {w.nv} RHS per step"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def rel_err_sampled(w, f_np, u_dev, count, seed=4096):
+    import oracle
+    rows = W.sample_targets(w, count, seed=seed)
+    ref = oracle.workload_apply(w, f_np, rows)
+    u = u_dev.reshape(-1, w.nv)[torch.from_numpy(rows).cuda()].cpu().to(torch.complex128).numpy()
+    return float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        reference_arm(args, ws, rank)
+        return
+    torch.cuda.set_device(local)
+    import paper_2411_03029_gb300 as tb
+    tb.build.build()
+    w = workload(args)
+    prec = args.precision if args.precision is not None else (
+        tb.PREC_C64 if w.precision == tb.PREC_C64_SPLITBF16 else w.precision)
+    mask = (1 << prec) | ((1 << tb.PREC_C128) if not args.no_fp64 else 0)
+    op = tb.from_workload(w, precisions=mask, use_graphs=not args.profile_only, precision=prec)
+    info = op.info()
+    nv = w.nv
+    f_host = W.rhs(w)                       # complex128, CPU
+    if ws > 1:                              # each replica applies its own batch
+        f_host = W.complex_gaussian(f_host.shape, 10_000 + rank)
+    dt = tb.dtype_of(prec)
+    f = f_host.to(dt).cuda()
+    u = torch.empty_like(f)
+    stream = torch.cuda.Stream()
+    N = w.N
+
+    if args.profile_only:
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup + args.steps):
+                op.apply(f, prec, out=u)
+        stream.synchronize()
+        print(json.dumps({"profile_only": True, "workload": w.name}))
+        return
+
+    # ---------------------------------------------------- timed region (graph replay)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            op.apply(f, prec, out=u)
+    stream.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(ws)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for _ in range(args.steps):
+                op.apply(f, prec, out=u)
+            ev1.record(stream)
+        stream.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        # the same K steps launched eagerly (legacy stream: no graph) with CUDA
+        # events recorded around every pass on that stream (roofline)
+        op.profile(True)
+        for _ in range(args.steps):
+            tb._check(tb.lib().tb_apply(op._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                        nv, prec, ctypes.c_void_p(0)))
+        torch.cuda.synchronize()
+        op.profile(False)
+    stats = op.profile_stats()
+    ms = max_over_ranks(ws, ms)
+    value = ws * N * nv / (ms * 1e-3) / 1e9
+    launches_per_step = 2 * info["Lc"] + 3
+
+    pk = peaks()
+    dom = max(stats, key=lambda s: s["ms_total"]) if stats else None
+    roof = None
+    if dom:
+        per_launch_ms = dom["ms_total"] / dom["launches"]
+        ai = dom["flops"] / max(dom["bytes"], 1)
+        achieved_gbs = dom["bytes"] / (per_launch_ms * 1e-3) / 1e9
+        roof = {"kernel": f'{dom["name"]}@l{dom["level"]}', "bound": "hbm", "achieved": achieved_gbs,
+                "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": achieved_gbs / pk["hbm_gbs"],
+                "peak_source": pk["source"], "traffic": None, "bytes_per_launch": dom["bytes"],
+                "flops_per_launch": dom["flops"], "ms_per_launch": per_launch_ms,
+                "tflops": dom["flops"] / (per_launch_ms * 1e-3) / 1e12, "flop_per_byte": ai,
+                "share_of_step": dom["ms_total"] / max(sum(s["ms_total"] for s in stats), 1e-9)}
+    passes = [{"pass": f'{s["name"]}@l{s["level"]}', "ms": s["ms_total"] / s["launches"],
+               "GBps": s["bytes"] / (s["ms_total"] / s["launches"] * 1e-3) / 1e9,
+               "TFLOPs": s["flops"] / (s["ms_total"] / s["launches"] * 1e-3) / 1e12} for s in stats]
+
+    # --------------------------------------------------- end to end with host buffers
+    f_pin = f_host.to(dt).pin_memory().numpy()
+    u_pin = torch.empty(f_pin.shape, dtype=dt).pin_memory().numpy()
+
+    tb._check(tb.lib().tb_apply_host(op._h, ctypes.c_void_p(f_pin.ctypes.data), ctypes.c_void_p(u_pin.ctypes.data),
+                                     nv, prec))
+    barrier(ws)
+    t0 = time.perf_counter()
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(e2e_steps):
+        tb._check(tb.lib().tb_apply_host(op._h, ctypes.c_void_p(f_pin.ctypes.data),
+                                         ctypes.c_void_p(u_pin.ctypes.data), nv, prec))
+    t_e2e = max_over_ranks(ws, (time.perf_counter() - t0) / e2e_steps)
+    es = 16 if prec == tb.PREC_C128 else 8
+    e2e = {"value": ws * N * nv / t_e2e / 1e9, "unit": UNIT, "h2d_bytes_per_step": N * nv * es,
+           "d2h_bytes_per_step": N * nv * es, "ms_per_step": t_e2e * 1e3}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": {0: "c128", 1: "c64", 2: "c64+bf16x2"}[prec], "data": "synthetic",
+           "config": {"workload": w.name, "kernel": w.description, "d": w.d, "n": w.n, "nv": nv, "tol": w.tol,
+                      "L": info["L"], "ranks_src": info["rank_src"], "ranks_tgt": info["rank_tgt"],
+                      "rank_min": info["rank_min"], "rank_max": info["rank_max"],
+                      "core_entries": info["core_entries"], "build_s": info["build_seconds"],
+                      "l2": "inputs larger than L2 (no flush)", "graph": True},
+           "roofline": roof, "passes": passes, "e2e": e2e,
+           "gpu_launches": launches_per_step * args.steps}
+
+    if rank == 0:
+        f_np = f_host.numpy()
+        if args.err_samples > 0:
+            out["rel_err_sampled"] = rel_err_sampled(w, f_np, u, args.err_samples)
+            out["rel_err_bound"] = w.bound
+        if not args.no_fp64 and prec != tb.PREC_C128:
+            f64 = f_host.cuda()
+            u64 = torch.empty_like(f64)
+            with torch.cuda.stream(stream):
+                op.apply(f64, tb.PREC_C128, out=u64)
+                stream.synchronize()
+                k64 = max(1, min(3, args.steps))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(k64):
+                    op.apply(f64, tb.PREC_C128, out=u64)
+                e1.record(stream)
+            stream.synchronize()
+            ms64 = e0.elapsed_time(e1) / k64
+            out["fp64_plain"] = {"value": N * nv / (ms64 * 1e-3) / 1e9, "ms_per_step": ms64,
+                                 "rel_err_sampled": rel_err_sampled(w, f_np, u64, args.err_samples)
+                                 if args.err_samples > 0 else None}
+            del f64, u64
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(w, f_np)
+    out["clocks"] = clk.summary()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    op.close()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

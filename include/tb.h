@@ -1,0 +1,212 @@
+/*
+ * tb.h -- C ABI of the GB300 tensor butterfly library.
+ *
+ * The library compresses a d-dimensional oscillatory integral operator
+ *     u(x^i) = sum_j K(x^i, y^j) f(y^j)
+ * discretized on tensor grids (a 2d-mode kernel tensor with n^{2d} entries, never
+ * formed) into a tensor butterfly, then applies it in O(n^d) work per right-hand
+ * side.  Reference: Kielstra, Shi, Luo, Qian, Liu, "A Linear-complexity Tensor
+ * Butterfly Algorithm for Compressing High-dimensional Oscillatory Integral
+ * Operators" (arXiv 2411.03029):
+ *   - construction: Alg. 1 (Sec. 3.2), built on the Tucker-type ID of Sec. 3.1;
+ *   - contraction (apply): Alg. 2 (Sec. 3.2), G = K x_{d+1..2d} F;
+ *   - adjoint: the conjugate transpose of the factorization of Eq. (butterfly_tensor).
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns a tb_status and never aborts or exits.  On failure,
+ *     tb_last_error() returns a message for the calling thread.
+ *   - Complex arrays are interleaved (re, im) pairs: complex128 for
+ *     TB_PREC_C128, complex64 for TB_PREC_C64 and TB_PREC_C64_SPLITBF16.
+ *   - Data layout of the input F and output G: C order over (n_1, ..., n_d, nv),
+ *     i.e. the right-hand-side index is innermost and axis 1 is slowest.  This
+ *     is the paper's F in C^{n_1 x ... x n_d x n_v} (Alg. 2 input) read in C order.
+ *   - Grid point i = (i_1..i_d) has coordinates (x_1[i_1], ..., x_d[i_d]).
+ *   - Ownership: a handle owns all device memory it allocates (factors, cores,
+ *     workspaces, CUDA graphs).  The caller owns f / u / g / v.
+ *   - Threading: a handle may be used from one host thread at a time.
+ *     Distinct handles are independent.
+ */
+#ifndef TB_H
+#define TB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TB_MAX_D 6       /* largest supported dimension d */
+#define TB_MAX_LEVELS 16 /* largest supported tree depth L */
+
+typedef enum {
+    TB_OK = 0,
+    TB_EINVAL = 1,        /* invalid argument (sizes, pointers, aliasing, grid) */
+    TB_ENOMEM = 2,        /* device or host allocation failed */
+    TB_ECUDA = 3,         /* a CUDA runtime call failed */
+    TB_ERANK = 4,         /* an ID needed more than the rank cap */
+    TB_ETIMEOUT = 5,      /* a bounded device wait expired */
+    TB_EUNSUPPORTED = 6   /* the request is valid but not built (precision, size) */
+} tb_status;
+
+/* Kernel families of the paper's numerical examples (Sec. 4). */
+typedef enum {
+    TB_KERNEL_FOURIER = 1,   /* K = exp(-2 pi i x.y)                        (Sec. 4.3) */
+    TB_KERNEL_HELMHOLTZ = 2, /* K = exp(i kappa |x-y|)/|x-y|, params[0]=kappa (Sec. 4.1) */
+    TB_KERNEL_RADON = 3      /* K = exp(2 pi i (x.xi + c(x)|xi|)),
+                                c(x) = params[0] + params[1] prod_k sin(2 pi x_k) (Sec. 4.2) */
+} tb_kernel_kind;
+
+typedef enum {
+    TB_PREC_C128 = 0,          /* complex128 data, FP64 arithmetic ("plain FP64") */
+    TB_PREC_C64 = 1,           /* complex64 data, FP32 arithmetic */
+    TB_PREC_C64_SPLITBF16 = 2  /* complex64 data; mid-level cores as two-term split
+                                  BF16 on the tensor cores with FP32 accumulation */
+} tb_precision;
+
+typedef enum {
+    TB_ORDER_AUTO = -1,    /* bit-reversed for FOURIER, natural otherwise */
+    TB_ORDER_NATURAL = 0,  /* tree nodes are contiguous index ranges (Sec. 3.2) */
+    TB_ORDER_BITREV = 1    /* bit-reversal ordering of each axis (Sec. 4.3) */
+} tb_order;
+
+typedef struct {
+    int kind;          /* tb_kernel_kind */
+    double params[4];  /* see tb_kernel_kind; unused entries ignored */
+} tb_kernel;
+
+/* Host pointers to per-axis coordinates: x[k] has n[k] target coordinates and
+   y[k] has n[k] source coordinates (the paper's m_k = n_k, Sec. 3.2).  Copied
+   during tb_build; the caller keeps ownership. */
+typedef struct {
+    const double *x[TB_MAX_D];
+    const double *y[TB_MAX_D];
+} tb_grids;
+
+typedef struct {
+    int L;                 /* tree levels per axis: even, n_k = C_b,k 2^L; -1 = planner's choice */
+    int order;             /* tb_order */
+    int proxy_rows;        /* row cap of each proxy matrix (power of two); 0 = 1024 */
+    int rank_max;          /* rank cap of each ID (<= 32); 0 = 32; exceeded -> TB_ERANK */
+    unsigned precisions;   /* bit mask of (1 << tb_precision) to prepare; 0 = all */
+    int separable;         /* -1 = by kernel (FOURIER), 0 = off, 1 = on */
+    int use_graphs;        /* 1 = replay each (f, u, nv, precision) apply as a CUDA graph */
+    int device;            /* CUDA device ordinal; -1 = the current device */
+    uint64_t seed;         /* seed of the proxy-row design (Sec. 2.1 proxy strategy) */
+} tb_options;
+
+typedef struct tb_plan *tb_handle;
+
+typedef struct {
+    int d;
+    int L;                         /* levels per tree */
+    int Lc;                        /* middle level L/2 */
+    int order;                     /* tb_order used */
+    int separable;                 /* 1 if per-mode (Kronecker) factors are used */
+    int64_t n[TB_MAX_D];           /* points per axis */
+    int64_t cb[TB_MAX_D];          /* leaf size per axis (C_b) */
+    int rank_src[TB_MAX_LEVELS][TB_MAX_D]; /* padded rank R_{l,k} of V/W, l = 0..Lc */
+    int rank_tgt[TB_MAX_LEVELS][TB_MAX_D]; /* padded rank of U/P, l = 0..Lc */
+    int rank_min;                  /* smallest rank over all IDs (Tables 2/3 r_min) */
+    int rank_max;                  /* largest rank over all IDs (Tables 2/3 r) */
+    int64_t num_ids;               /* IDs computed during construction */
+    int64_t core_entries;          /* entries of all mid-level cores K(t-bar, s-bar) */
+    int64_t factor_entries;        /* entries of all V, W, U, P blocks (padded) */
+    int64_t level_entries_max;     /* largest intermediate (per RHS, padded) */
+    int64_t device_bytes;          /* device memory held by the handle */
+    double build_seconds;          /* wall time of tb_build */
+} tb_info;
+
+/* Fill *opt with the defaults described in tb_options. */
+tb_status tb_options_default(tb_options *opt);
+
+/*
+ * Construct the tensor butterfly of K on the given grids (Alg. 1, Sec. 3.2).
+ *   kernel  kernel family and parameters (host pointer, read during the call)
+ *   d       dimension, 1 <= d <= TB_MAX_D (the paper's d > 1; d = 1 is the
+ *           matrix butterfly, Sec. 3.2)
+ *   n       n[k] points per axis on each side; n[k] = C_b,k 2^L, power of two
+ *   grids   host coordinate arrays (copied)
+ *   tol     relative ID tolerance epsilon of Sec. 2.1, 0 < tol < 1
+ *   out     receives the handle (NULL on failure)
+ * Factors are computed on the current CUDA device in FP64 (kernel phases,
+ * column-pivoted QR, triangular solves) and stored in the precisions requested.
+ * Errors: TB_EINVAL for bad sizes/pointers or coincident Helmholtz points,
+ * TB_ERANK if an ID needs more than the rank cap, TB_ENOMEM, TB_ECUDA.
+ */
+tb_status tb_build(const tb_kernel *kernel, int d, const int64_t *n,
+                   const tb_grids *grids, double tol, tb_handle *out);
+
+/* tb_build with explicit options (NULL = defaults). */
+tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *n,
+                      const tb_grids *grids, double tol, const tb_options *opt,
+                      tb_handle *out);
+
+/*
+ * u = K f (Alg. 2): device pointers f (input, prod n x nv) and u (output),
+ * element type per `precision`, layout C order (n_1..n_d, nv).  Stream-ordered
+ * on `cuda_stream` (a cudaStream_t; NULL = legacy default stream); returns
+ * after the launches are enqueued.  f and u must not overlap (TB_EINVAL).
+ * TB_EUNSUPPORTED if the handle was built without `precision`.
+ */
+tb_status tb_apply(tb_handle h, const void *f, void *u, int64_t nv, int precision,
+                   void *cuda_stream);
+
+/*
+ * v = K^H g: the adjoint apply (conjugate transpose of Eq. butterfly_tensor,
+ * factors traversed in reverse).  Same conventions as tb_apply; g has the
+ * target-grid shape, v the source-grid shape.
+ */
+tb_status tb_apply_adjoint(tb_handle h, const void *g, void *v, int64_t nv, int precision,
+                           void *cuda_stream);
+
+/*
+ * u = K f with HOST buffers: copies f to the device, applies, and copies u back
+ * before returning (synchronous).  f and u are host pointers of the tb_apply
+ * layout; pinned memory gives the best transfer rate.  Device staging buffers
+ * are owned by the handle.
+ */
+tb_status tb_apply_host(tb_handle h, const void *f, void *u, int64_t nv, int precision);
+
+/* Describe a built handle (ranks, sizes, timings). */
+tb_status tb_query(tb_handle h, tb_info *info);
+
+/* Per-pass timing of eager applies (not of CUDA-graph replays). */
+typedef struct {
+    char name[24];          /* "leaf_in", "split", "core", "gather", "leaf_out" */
+    int level;              /* tree level of the pass (core: Lc) */
+    int adjoint;            /* 1 for passes of tb_apply_adjoint */
+    int64_t launches;       /* kernel launches recorded */
+    double ms_total;        /* summed device time of those launches (CUDA events) */
+    int64_t bytes;          /* bytes one launch must move: its inputs, outputs and
+                               factors at their stored sizes */
+    double flops;           /* real floating-point operations of one launch */
+} tb_pass_stat;
+
+/*
+ * Enable (on = 1) or disable per-pass timing: while enabled, every eager
+ * apply records a CUDA event pair around each kernel launch on the apply's
+ * stream.  Events add no work to the kernels themselves.
+ */
+tb_status tb_profile_enable(tb_handle h, int on);
+
+/*
+ * Synchronize the recorded events, aggregate them by (name, level, adjoint)
+ * into stats[0 .. *count) (at most `cap` entries, host memory) and clear the
+ * record.
+ */
+tb_status tb_profile_stats(tb_handle h, tb_pass_stat *stats, int cap, int *count);
+
+/* Release everything the handle owns.  NULL is accepted (TB_OK). */
+tb_status tb_free(tb_handle h);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *tb_last_error(void);
+
+/* Library version string. */
+const char *tb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TB_H */

@@ -1,0 +1,290 @@
+"""GB300 tensor butterfly: Python binding of the C ABI in include/tb.h.
+
+Argument marshalling only: every step of construction and apply runs in the
+CUDA library libtb.so (built by paper_2411_03029_gb300.build).  There is no CPU
+fallback; a missing library raises.
+
+  op = TBOperator(kind, d, n, xs, ys, tol, params=...)   # tb_build_ex (Alg. 1)
+  u = op.apply(f)                                        # tb_apply   (Alg. 2), torch CUDA tensor
+  v = op.apply_adjoint(g)                                # tb_apply_adjoint (K^H)
+  u = apply(op, f)                                       # autograd: backward = adjoint apply
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+TB_MAX_D = 6
+TB_MAX_LEVELS = 16
+
+KERNEL_FOURIER, KERNEL_HELMHOLTZ, KERNEL_RADON = 1, 2, 3
+PREC_C128, PREC_C64, PREC_C64_SPLITBF16 = 0, 1, 2
+ORDER_AUTO, ORDER_NATURAL, ORDER_BITREV = -1, 0, 1
+
+STATUS = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "TB_ERANK",
+          5: "TB_ETIMEOUT", 6: "TB_EUNSUPPORTED"}
+
+# every symbol declared in include/tb.h
+EXPORTS = ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
+           "tb_apply_host", "tb_query", "tb_free", "tb_last_error", "tb_version",
+           "tb_profile_enable", "tb_profile_stats")
+
+
+class TBError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Kernel(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("params", ctypes.c_double * 4)]
+
+
+class _Grids(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p * TB_MAX_D), ("y", ctypes.c_void_p * TB_MAX_D)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("order", ctypes.c_int), ("proxy_rows", ctypes.c_int),
+                ("rank_max", ctypes.c_int), ("precisions", ctypes.c_uint), ("separable", ctypes.c_int),
+                ("use_graphs", ctypes.c_int), ("device", ctypes.c_int), ("seed", ctypes.c_uint64)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("L", ctypes.c_int), ("Lc", ctypes.c_int), ("order", ctypes.c_int),
+                ("separable", ctypes.c_int), ("n", ctypes.c_int64 * TB_MAX_D), ("cb", ctypes.c_int64 * TB_MAX_D),
+                ("rank_src", (ctypes.c_int * TB_MAX_D) * TB_MAX_LEVELS),
+                ("rank_tgt", (ctypes.c_int * TB_MAX_D) * TB_MAX_LEVELS),
+                ("rank_min", ctypes.c_int), ("rank_max", ctypes.c_int), ("num_ids", ctypes.c_int64),
+                ("core_entries", ctypes.c_int64), ("factor_entries", ctypes.c_int64),
+                ("level_entries_max", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("build_seconds", ctypes.c_double)]
+
+
+class _PassStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 24), ("level", ctypes.c_int), ("adjoint", ctypes.c_int),
+                ("launches", ctypes.c_int64), ("ms_total", ctypes.c_double), ("bytes", ctypes.c_int64),
+                ("flops", ctypes.c_double)]
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libtb.so.  Raises if it has not been built: there is no fallback."""
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library {path} is missing; build it with "
+                               "paper_2411_03029_gb300.build.build() (nvcc, sm_103a)")
+        L = ctypes.CDLL(path)
+        P, I64 = ctypes.c_void_p, ctypes.c_int64
+        L.tb_options_default.argtypes = [ctypes.POINTER(_Options)]
+        L.tb_build.argtypes = [ctypes.POINTER(_Kernel), ctypes.c_int, P, ctypes.POINTER(_Grids), ctypes.c_double,
+                               ctypes.POINTER(P)]
+        L.tb_build_ex.argtypes = [ctypes.POINTER(_Kernel), ctypes.c_int, P, ctypes.POINTER(_Grids), ctypes.c_double,
+                                  ctypes.POINTER(_Options), ctypes.POINTER(P)]
+        L.tb_apply.argtypes = [P, P, P, I64, ctypes.c_int, P]
+        L.tb_apply_adjoint.argtypes = [P, P, P, I64, ctypes.c_int, P]
+        L.tb_apply_host.argtypes = [P, P, P, I64, ctypes.c_int]
+        L.tb_query.argtypes = [P, ctypes.POINTER(_Info)]
+        L.tb_free.argtypes = [P]
+        L.tb_last_error.argtypes = []
+        L.tb_last_error.restype = ctypes.c_char_p
+        L.tb_version.argtypes = []
+        L.tb_version.restype = ctypes.c_char_p
+        L.tb_profile_enable.argtypes = [P, ctypes.c_int]
+        L.tb_profile_stats.argtypes = [P, ctypes.POINTER(_PassStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        for name in ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
+                     "tb_apply_host", "tb_query", "tb_free", "tb_profile_enable", "tb_profile_stats"):
+            getattr(L, name).restype = ctypes.c_int
+        _LIB = L
+    return _LIB
+
+
+def _check(status: int):
+    if status != 0:
+        raise TBError(status, lib().tb_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_of(precision: int):
+    torch = _torch()
+    return torch.complex128 if precision == PREC_C128 else torch.complex64
+
+
+class TBOperator:
+    """A tensor butterfly of K on tensor grids, built on the current CUDA device."""
+
+    def __init__(self, kind: int, d: int, n, xs, ys, tol: float, params=(), L: int = -1,
+                 order: int = ORDER_AUTO, precisions: int = 0, separable: int = -1,
+                 use_graphs: bool = False, proxy_rows: int = 1024, rank_max: int = 32,
+                 seed: int = 0x5eed, precision: int = PREC_C64):
+        L_ = lib()
+        n = [int(v) for v in (n if np.iterable(n) else [n] * d)]
+        self.d, self.n, self.kind = d, n, kind
+        self.precision = precision
+        self._xs = [np.ascontiguousarray(x, dtype=np.float64) for x in xs]
+        self._ys = [np.ascontiguousarray(y, dtype=np.float64) for y in ys]
+        kern = _Kernel(kind, (ctypes.c_double * 4)(*(list(params) + [0.0] * (4 - len(params)))))
+        grids = _Grids()
+        for k in range(d):
+            grids.x[k] = self._xs[k].ctypes.data
+            grids.y[k] = self._ys[k].ctypes.data
+        opt = _Options()
+        _check(L_.tb_options_default(ctypes.byref(opt)))
+        opt.L, opt.order, opt.proxy_rows, opt.rank_max = L, order, proxy_rows, rank_max
+        opt.precisions, opt.separable, opt.use_graphs, opt.seed = precisions, separable, int(use_graphs), seed
+        try:
+            opt.device = _torch().cuda.current_device()
+        except Exception:  # pragma: no cover
+            opt.device = -1
+        narr = (ctypes.c_int64 * d)(*n)
+        h = ctypes.c_void_p()
+        _check(L_.tb_build_ex(ctypes.byref(kern), d, ctypes.cast(narr, ctypes.c_void_p), ctypes.byref(grids),
+                              float(tol), ctypes.byref(opt), ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def N(self) -> int:
+        return int(np.prod(self.n))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().tb_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        inf = _Info()
+        _check(lib().tb_query(self._h, ctypes.byref(inf)))
+        Lc = inf.Lc
+        return {
+            "d": inf.d, "L": inf.L, "Lc": Lc, "order": inf.order, "separable": inf.separable,
+            "n": list(inf.n[: inf.d]), "cb": list(inf.cb[: inf.d]),
+            "rank_src": [list(inf.rank_src[l][: inf.d]) for l in range(Lc + 1)],
+            "rank_tgt": [list(inf.rank_tgt[l][: inf.d]) for l in range(Lc + 1)],
+            "rank_min": inf.rank_min, "rank_max": inf.rank_max, "num_ids": inf.num_ids,
+            "core_entries": inf.core_entries, "factor_entries": inf.factor_entries,
+            "level_entries_max": inf.level_entries_max, "device_bytes": inf.device_bytes,
+            "build_seconds": inf.build_seconds,
+        }
+
+    def profile(self, on: bool = True):
+        """Record CUDA events around every pass of eager applies (tb_profile_enable)."""
+        _check(lib().tb_profile_enable(self._h, int(on)))
+
+    def profile_stats(self) -> list:
+        """Per-pass launches, device time, bytes and flops since the last call."""
+        arr = (_PassStat * 64)()
+        cnt = ctypes.c_int()
+        _check(lib().tb_profile_stats(self._h, arr, 64, ctypes.byref(cnt)))
+        return [{"name": a.name.decode(), "level": a.level, "adjoint": a.adjoint, "launches": a.launches,
+                 "ms_total": a.ms_total, "bytes": a.bytes, "flops": a.flops} for a in arr[: cnt.value]]
+
+    def _prep(self, x, precision):
+        torch = _torch()
+        precision = self.precision if precision is None else precision
+        dt = dtype_of(precision)
+        if not isinstance(x, torch.Tensor) or not x.is_cuda:
+            raise TypeError("expected a CUDA torch tensor")
+        if x.dtype != dt:
+            raise TypeError(f"precision {precision} needs dtype {dt}, got {x.dtype}")
+        squeeze = x.dim() == self.d
+        if squeeze:
+            x = x.unsqueeze(-1)
+        if tuple(x.shape[: self.d]) != tuple(self.n) or x.dim() != self.d + 1:
+            raise ValueError(f"expected shape {tuple(self.n)} + (nv,), got {tuple(x.shape)}")
+        if not x.is_contiguous():
+            x = x.contiguous()
+        return x, precision, squeeze
+
+    def _run(self, fn, x, precision, out):
+        torch = _torch()
+        x, precision, squeeze = self._prep(x, precision)
+        nv = x.shape[-1]
+        if out is None:
+            out = torch.empty_like(x)
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        _check(fn(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()), nv, precision,
+                  ctypes.c_void_p(stream)))
+        return out.squeeze(-1) if squeeze else out
+
+    def apply(self, f, precision: int | None = None, out=None):
+        """u = K f on the current torch stream (tb_apply)."""
+        return self._run(lib().tb_apply, f, precision, out)
+
+    def apply_adjoint(self, g, precision: int | None = None, out=None):
+        """v = K^H g on the current torch stream (tb_apply_adjoint)."""
+        return self._run(lib().tb_apply_adjoint, g, precision, out)
+
+    def apply_host(self, f: np.ndarray, precision: int | None = None) -> np.ndarray:
+        """u = K f with host arrays; copies in and out inside the call (tb_apply_host)."""
+        precision = self.precision if precision is None else precision
+        dt = np.complex128 if precision == PREC_C128 else np.complex64
+        f = np.ascontiguousarray(f, dtype=dt)
+        nv = f.shape[-1] if f.ndim == self.d + 1 else 1
+        u = np.empty_like(f)
+        _check(lib().tb_apply_host(self._h, ctypes.c_void_p(f.ctypes.data), ctypes.c_void_p(u.ctypes.data),
+                                   nv, precision))
+        return u
+
+
+def from_workload(w, **kw) -> TBOperator:
+    """Build the operator of a workloads.Workload (grids, kernel, tolerance, order)."""
+    import workloads
+    xs, ys = workloads.grids(w)
+    kw.setdefault("L", w.L)
+    kw.setdefault("order", w.order)
+    kw.setdefault("precision", w.precision)
+    return TBOperator(w.kind, w.d, [w.n] * w.d, xs, ys, w.tol, params=w.params, **kw)
+
+
+def _autograd_fn():
+    torch = _torch()
+
+    class TBApply(torch.autograd.Function):
+        """u = K f with the adjoint butterfly as its backward.
+
+        For a linear map, PyTorch's complex convention passes grad_u = dL/dRe(u)
+        + i dL/dIm(u) and expects dL/dRe(f) + i dL/dIm(f) = K^H grad_u."""
+
+        @staticmethod
+        def forward(ctx, f, op, precision):
+            ctx.op, ctx.precision = op, precision
+            return op.apply(f.detach(), precision)
+
+        @staticmethod
+        def backward(ctx, gu):
+            return ctx.op.apply_adjoint(gu.contiguous(), ctx.precision), None, None
+
+    return TBApply
+
+
+_TBApply = None
+
+
+def apply(op: TBOperator, f, precision: int | None = None):
+    """Differentiable u = K f (backward: v = K^H grad_u through tb_apply_adjoint)."""
+    global _TBApply
+    if _TBApply is None:
+        _TBApply = _autograd_fn()
+    return _TBApply.apply(f, op, op.precision if precision is None else precision)

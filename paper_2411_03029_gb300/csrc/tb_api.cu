@@ -1,0 +1,917 @@
+// C ABI of the tensor butterfly library: argument checks, planning,
+// construction orchestration (Alg. 1) and apply orchestration (Alg. 2).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tb_kernels.cuh"
+#include "tb_plan.cuh"
+
+using namespace tb;
+
+static thread_local std::string g_err;
+
+// apply precisions this library implements (bit i = tb_precision i)
+static const unsigned TB_PRECISIONS_BUILT = (1u << TB_PREC_C128) | (1u << TB_PREC_C64);
+
+static tb_status fail(tb_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+#define TB_CK(call)                                                                              \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            return fail(e_ == cudaErrorMemoryAllocation ? TB_ENOMEM : TB_ECUDA,                  \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+        }                                                                                        \
+    } while (0)
+
+#define TB_TRY(expr)                      \
+    do {                                  \
+        tb_status s_ = (expr);            \
+        if (s_ != TB_OK) return s_;       \
+    } while (0)
+
+namespace {
+
+size_t g_smem_optin = 0;
+
+bool pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+int ilog2(int64_t x) {
+    int r = 0;
+    while ((int64_t(1) << r) < x) ++r;
+    return r;
+}
+
+template <class T>
+tb_status dalloc(tb_plan *h, T **p, int64_t count) {
+    *p = nullptr;
+    if (count <= 0) return TB_OK;
+    cudaError_t e = cudaMalloc((void **)p, (size_t)count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TB_ENOMEM, "cudaMalloc of " + std::to_string((size_t)count * sizeof(T)) + " bytes failed");
+    }
+    h->allocations.push_back((void *)*p);
+    h->device_bytes += (int64_t)count * sizeof(T);
+    return TB_OK;
+}
+
+void dfree(tb_plan *h, void *p) {
+    if (!p) return;
+    auto it = std::find(h->allocations.begin(), h->allocations.end(), p);
+    if (it != h->allocations.end()) h->allocations.erase(it);
+    cudaFree(p);
+}
+
+int64_t prod_tile(const SideLevel &s, int d) {
+    int64_t t = 1;
+    for (int k = 0; k < d; ++k) t *= s.R[k];
+    return t;
+}
+
+tb_status check_device_ptr(const void *p, const char *what) {
+    if (!p) return fail(TB_EINVAL, std::string(what) + " is NULL");
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TB_EINVAL, std::string(what) + " is not a CUDA pointer");
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(TB_EINVAL, std::string(what) + " is not device memory");
+    return TB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *tb_last_error(void) { return g_err.c_str(); }
+const char *tb_version(void) { return "tb 0.1 (sm_103a)"; }
+
+tb_status tb_options_default(tb_options *o) {
+    if (!o) return fail(TB_EINVAL, "options pointer is NULL");
+    o->L = -1;
+    o->order = TB_ORDER_AUTO;
+    o->proxy_rows = 1024;
+    o->rank_max = 32;
+    o->precisions = 0;
+    o->separable = -1;
+    o->use_graphs = 0;
+    o->device = -1;
+    o->seed = 0x5eed;
+    return TB_OK;
+}
+
+tb_status tb_free(tb_handle h) {
+    if (!h) return TB_OK;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    for (void *p : h->allocations) cudaFree(p);
+    if (h->ws.buf[0]) cudaFree(h->ws.buf[0]);
+    if (h->ws.buf[1]) cudaFree(h->ws.buf[1]);
+    if (h->ws.host_in) cudaFree(h->ws.host_in);
+    if (h->ws.host_out) cudaFree(h->ws.host_out);
+    cudaSetDevice(cur);
+    delete h;
+    return TB_OK;
+}
+
+}  // extern "C"
+
+// -------------------------------------------------------------- construction
+static tb_status build_side(tb_plan *h, int side) {
+    const int d = h->d, Lc = h->Lc;
+    const int64_t nF = ipow2(d * Lc);
+    SideLevel *lv = side == 0 ? h->src : h->tgt;
+    for (int l = 0; l <= Lc; ++l) {
+        SideLevel &S = lv[l];
+        const int64_t nM = ipow2(d * l);
+        const int nseg = 1 << (Lc - l);
+        IdArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.side = side;
+        a.d = d;
+        a.l = l;
+        a.Lc = Lc;
+        a.separable = h->separable;
+        a.ks = h->ks;
+        a.rows_cap = h->proxy_rows;
+        a.rows_bits = ilog2(h->proxy_rows);
+        a.tol = h->tol;
+        a.rank_max = h->rank_max;
+        a.seed = (uint32_t)(h->seed ^ (h->seed >> 32));
+        a.err = h->d_err;
+        int ncmax = 0;
+        for (int k = 0; k < d; ++k) {
+            a.n[k] = (int)h->n[k];
+            a.cb[k] = (int)h->cb[k];
+            a.perm[k] = h->perm[k];
+            a.own[k] = side == 0 ? h->ys[k] : h->xs[k];
+            a.oth[k] = side == 0 ? h->xs[k] : h->ys[k];
+            S.cin[k] = l == 0 ? (int)h->cb[k] : 2 * lv[l - 1].R[k];
+            S.cap[k] = std::min(S.cin[k], h->rank_max);
+            S.count[k] = h->separable ? ipow2(h->L) : nF * nM * nseg;
+            ncmax = std::max(ncmax, S.cin[k]);
+            if (l > 0) {
+                a.pskel[k] = lv[l - 1].skel[k];
+                a.prank[k] = lv[l - 1].rank[k];
+                a.pcap[k] = lv[l - 1].cap[k];
+                a.pR[k] = lv[l - 1].R[k];
+            }
+        }
+        if (ncmax > id_max_columns())
+            return fail(TB_ERANK, "level " + std::to_string(l) + " needs " + std::to_string(ncmax) +
+                                      " candidate columns; the ID kernel holds at most " +
+                                      std::to_string(id_max_columns()));
+        a.ncmax = ncmax;
+        for (int k = 0; k < d; ++k) {
+            TB_TRY(dalloc(h, &S.fac64[k], S.count[k] * S.cap[k] * S.cin[k]));
+            TB_TRY(dalloc(h, &S.skel[k], S.count[k] * S.cap[k]));
+            TB_TRY(dalloc(h, &S.rank[k], S.count[k]));
+            a.fac[k] = S.fac64[k];
+            a.skel[k] = S.skel[k];
+            a.rank[k] = S.rank[k];
+            a.cap[k] = S.cap[k];
+            a.cin[k] = S.cin[k];
+        }
+        a.nids = h->separable ? (int64_t)d * ipow2(h->L) : nF * nM * d * nseg;
+        h->num_ids += a.nids;
+        TB_CK(launch_interp_decomp(a, 0));
+        TB_CK(cudaDeviceSynchronize());
+        int err = 0;
+        TB_CK(cudaMemcpy(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err == 2)
+            return fail(TB_ERANK, "an ID at level " + std::to_string(l) + " needs more than rank cap " +
+                                      std::to_string(h->rank_max) + " at tolerance " + std::to_string(h->tol));
+        // padded ranks R_{l,k} and rank statistics
+        S.rmin = 1 << 30;
+        S.rmax = 0;
+        for (int k = 0; k < d; ++k) {
+            std::vector<int> rk((size_t)S.count[k]);
+            TB_CK(cudaMemcpy(rk.data(), S.rank[k], rk.size() * sizeof(int), cudaMemcpyDeviceToHost));
+            int mx = 1, mn = 1 << 30;
+            for (int r : rk) { mx = std::max(mx, r); mn = std::min(mn, r); }
+            S.R[k] = mx;
+            S.rmin = std::min(S.rmin, mn);
+            S.rmax = std::max(S.rmax, mx);
+            if (S.R[k] < S.cap[k]) {   // drop the unused padding rows
+                c128 *packed = nullptr;
+                TB_TRY(dalloc(h, &packed, S.count[k] * S.R[k] * S.cin[k]));
+                const size_t w = (size_t)S.R[k] * S.cin[k] * sizeof(c128);
+                const size_t sp = (size_t)S.cap[k] * S.cin[k] * sizeof(c128);
+                TB_CK(cudaMemcpy2D(packed, w, S.fac64[k], sp, w, (size_t)S.count[k], cudaMemcpyDeviceToDevice));
+                dfree(h, S.fac64[k]);
+                h->device_bytes -= S.count[k] * S.cap[k] * S.cin[k] * (int64_t)sizeof(c128);
+                S.fac64[k] = packed;
+            }
+        }
+        h->rank_min = std::min(h->rank_min, S.rmin);
+        h->rank_max_seen = std::max(h->rank_max_seen, S.rmax);
+    }
+    return TB_OK;
+}
+
+static tb_status build_cores(tb_plan *h) {
+    const int d = h->d, Lc = h->Lc;
+    const int64_t nF = ipow2(d * Lc);
+    h->P = nF * nF;
+    const bool want64 = h->precisions & (1u << TB_PREC_C128);
+    const bool want32 = h->precisions & ((1u << TB_PREC_C64) | (1u << TB_PREC_C64_SPLITBF16));
+    SideLevel &T = h->tgt[Lc], &S = h->src[Lc];
+    if (h->separable) {
+        const int nb = 1 << Lc;
+        for (int k = 0; k < d; ++k) {
+            const int64_t cnt = (int64_t)nb * nb * T.R[k] * S.R[k];
+            if (want64) TB_TRY(dalloc(h, &h->kron64[k], cnt));
+            if (want32) TB_TRY(dalloc(h, &h->kron32[k], cnt));
+            KronArgs a;
+            a.Lc = Lc;
+            a.Rt = T.R[k];
+            a.Rs = S.R[k];
+            a.tcap = T.cap[k];
+            a.scap = S.cap[k];
+            a.trank = T.rank[k];
+            a.srank = S.rank[k];
+            a.tskel = T.skel[k];
+            a.sskel = S.skel[k];
+            a.xk = h->xs[k];
+            a.yk = h->ys[k];
+            a.ks = h->ks;
+            a.out64 = h->kron64[k];
+            a.out32 = h->kron32[k];
+            TB_CK(launch_kron_eval(a, 0));
+            h->core_entries += cnt;
+        }
+        TB_CK(cudaDeviceSynchronize());
+        return TB_OK;
+    }
+    std::vector<std::vector<int>> rt(d), rs(d);
+    for (int k = 0; k < d; ++k) {
+        rt[k].resize((size_t)T.count[k]);
+        rs[k].resize((size_t)S.count[k]);
+        TB_CK(cudaMemcpy(rt[k].data(), T.rank[k], rt[k].size() * sizeof(int), cudaMemcpyDeviceToHost));
+        TB_CK(cudaMemcpy(rs[k].data(), S.rank[k], rs[k].size() * sizeof(int), cudaMemcpyDeviceToHost));
+    }
+    std::vector<int> dims((size_t)h->P * 2 * d);
+    std::vector<int64_t> off((size_t)h->P + 1);
+    int64_t acc = 0;
+    for (int64_t p = 0; p < h->P; ++p) {
+        const int64_t t = p / nF, s = p % nF;
+        int64_t mt = 1, ms = 1;
+        for (int k = 0; k < d; ++k) {
+            const int a = rt[k][(size_t)(t * nF + s)], b = rs[k][(size_t)(s * nF + t)];
+            dims[(size_t)p * 2 * d + k] = a;
+            dims[(size_t)p * 2 * d + d + k] = b;
+            mt *= a;
+            ms *= b;
+        }
+        off[(size_t)p] = acc;
+        acc += mt * ms;
+        h->core_out_entries += mt;
+        h->core_in_entries += ms;
+    }
+    off[(size_t)h->P] = acc;
+    h->core_entries = acc;
+    TB_TRY(dalloc(h, &h->core_dims, (int64_t)dims.size()));
+    TB_TRY(dalloc(h, &h->core_off, (int64_t)off.size()));
+    TB_CK(cudaMemcpy(h->core_dims, dims.data(), dims.size() * sizeof(int), cudaMemcpyHostToDevice));
+    TB_CK(cudaMemcpy(h->core_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    if (want64) TB_TRY(dalloc(h, &h->core64, acc));
+    if (want32) TB_TRY(dalloc(h, &h->core32, acc));
+    CoreArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.d = d;
+    a.P = h->P;
+    a.nF = nF;
+    a.dims = h->core_dims;
+    a.off = h->core_off;
+    for (int k = 0; k < d; ++k) {
+        a.tskel[k] = T.skel[k];
+        a.sskel[k] = S.skel[k];
+        a.tcap[k] = T.cap[k];
+        a.scap[k] = S.cap[k];
+        a.xs[k] = h->xs[k];
+        a.ys[k] = h->ys[k];
+    }
+    a.ks = h->ks;
+    a.out64 = h->core64;
+    a.out32 = h->core32;
+    TB_CK(launch_core_eval(a, 0));
+    TB_CK(cudaDeviceSynchronize());
+    return TB_OK;
+}
+
+extern "C" tb_status tb_build(const tb_kernel *kernel, int d, const int64_t *n, const tb_grids *grids,
+                              double tol, tb_handle *out) {
+    return tb_build_ex(kernel, d, n, grids, tol, nullptr, out);
+}
+
+static tb_status build_impl(tb_plan *h, const tb_grids *grids) {
+    const int d = h->d;
+    TB_TRY(dalloc(h, &h->d_err, 1));
+    TB_CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    for (int k = 0; k < d; ++k) {
+        const int64_t nk = h->n[k];
+        TB_TRY(dalloc(h, &h->xs[k], nk));
+        TB_TRY(dalloc(h, &h->ys[k], nk));
+        TB_TRY(dalloc(h, &h->perm[k], nk));
+        TB_CK(cudaMemcpy(h->xs[k], grids->x[k], nk * sizeof(double), cudaMemcpyHostToDevice));
+        TB_CK(cudaMemcpy(h->ys[k], grids->y[k], nk * sizeof(double), cudaMemcpyHostToDevice));
+        std::vector<int> pm((size_t)nk);
+        const int bits = ilog2(nk);
+        for (int64_t p = 0; p < nk; ++p) {
+            int64_t q = p;
+            if (h->order == TB_ORDER_BITREV) {
+                q = 0;
+                for (int b = 0; b < bits; ++b) q |= ((p >> b) & 1) << (bits - 1 - b);
+            }
+            pm[(size_t)p] = (int)q;
+        }
+        TB_CK(cudaMemcpy(h->perm[k], pm.data(), pm.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    TB_TRY(build_side(h, 0));
+    TB_TRY(build_side(h, 1));
+    TB_TRY(build_cores(h));
+    // apply precisions of the factors
+    const bool want32 = h->precisions & ((1u << TB_PREC_C64) | (1u << TB_PREC_C64_SPLITBF16));
+    for (int side = 0; side < 2; ++side) {
+        SideLevel *lv = side == 0 ? h->src : h->tgt;
+        for (int l = 0; l <= h->Lc; ++l)
+            for (int k = 0; k < d; ++k) {
+                const int64_t cnt = lv[l].count[k] * lv[l].R[k] * lv[l].cin[k];
+                if (want32) {
+                    TB_TRY(dalloc(h, &lv[l].fac32[k], cnt));
+                    TB_CK(launch_to_c64(lv[l].fac64[k], lv[l].fac32[k], cnt, 0));
+                }
+            }
+    }
+    int64_t lm = 0;
+    for (int l = 0; l <= h->Lc; ++l) {
+        lm = std::max(lm, h->P * prod_tile(h->src[l], d));
+        lm = std::max(lm, h->P * prod_tile(h->tgt[l], d));
+    }
+    h->level_max = lm;
+    TB_CK(cudaDeviceSynchronize());
+    return TB_OK;
+}
+
+extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *n, const tb_grids *grids,
+                                 double tol, const tb_options *opt_in, tb_handle *out) {
+    if (!out) return fail(TB_EINVAL, "out handle pointer is NULL");
+    *out = nullptr;
+    if (!kernel || !n || !grids) return fail(TB_EINVAL, "kernel, n and grids must be non-NULL");
+    if (kernel->kind < TB_KERNEL_FOURIER || kernel->kind > TB_KERNEL_RADON)
+        return fail(TB_EINVAL, "unknown kernel kind " + std::to_string(kernel->kind));
+    if (d < 1 || d > TB_MAX_D) return fail(TB_EINVAL, "d must be in [1, " + std::to_string(TB_MAX_D) + "]");
+    if (!(tol > 0.0 && tol < 1.0)) return fail(TB_EINVAL, "tol must be in (0, 1)");
+    tb_options opt;
+    tb_options_default(&opt);
+    if (opt_in) opt = *opt_in;
+    for (int k = 0; k < d; ++k) {
+        if (!pow2(n[k]) || n[k] < 2) return fail(TB_EINVAL, "n[k] must be a power of two >= 2");
+        if (n[k] > (1 << 24)) return fail(TB_EINVAL, "n[k] too large");
+        if (!grids->x[k] || !grids->y[k]) return fail(TB_EINVAL, "grid pointer is NULL");
+    }
+    if (opt.proxy_rows <= 0) opt.proxy_rows = 1024;
+    if (!pow2(opt.proxy_rows) || opt.proxy_rows > (1 << 20)) return fail(TB_EINVAL, "proxy_rows must be a power of two");
+    if (opt.rank_max <= 0) opt.rank_max = 32;
+    if (opt.rank_max > id_max_columns() / 2) return fail(TB_EINVAL, "rank_max must be <= 32");
+    // coincident source/target points make the Helmholtz kernel singular
+    if (kernel->kind == TB_KERNEL_HELMHOLTZ) {
+        bool all_axes_meet = true;
+        for (int k = 0; k < d && all_axes_meet; ++k) {
+            std::vector<double> xa(grids->x[k], grids->x[k] + n[k]), ya(grids->y[k], grids->y[k] + n[k]);
+            std::sort(xa.begin(), xa.end());
+            std::sort(ya.begin(), ya.end());
+            std::vector<double> both;
+            std::set_intersection(xa.begin(), xa.end(), ya.begin(), ya.end(), std::back_inserter(both));
+            all_axes_meet = !both.empty();
+        }
+        if (all_axes_meet) return fail(TB_EINVAL, "Helmholtz kernel: a source point coincides with a target point");
+    }
+    // levels: n_k = C_b,k 2^L with L even
+    int L = opt.L;
+    int64_t nmin = n[0];
+    for (int k = 1; k < d; ++k) nmin = std::min(nmin, n[k]);
+    if (L < 0) {
+        // leaves of 4 points, or 16 for large 3-D grids, where larger leaves
+        // shrink the mid-level cores (their count grows as (n / C_b)^d)
+        const int64_t cbmin = (d == 3 && nmin >= 256) ? 16 : 4;
+        L = 0;
+        while ((nmin >> (L + 2)) >= cbmin) L += 2;
+    }
+    if (L % 2 != 0 || L < 0 || L >= TB_MAX_LEVELS || (nmin >> L) < 1)
+        return fail(TB_EINVAL, "L must be even with n_k / 2^L >= 1");
+    int dev = opt.device;
+    if (dev < 0) {
+        if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "no CUDA device"); }
+    }
+    if (cudaSetDevice(dev) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice failed"); }
+
+    auto t0 = std::chrono::steady_clock::now();
+    tb_plan *h = new tb_plan();
+    h->d = d;
+    h->L = L;
+    h->Lc = L / 2;
+    h->device = dev;
+    h->tol = tol;
+    h->order = opt.order == TB_ORDER_AUTO ? (kernel->kind == TB_KERNEL_FOURIER ? TB_ORDER_BITREV : TB_ORDER_NATURAL)
+                                          : opt.order;
+    h->separable = opt.separable < 0 ? (kernel->kind == TB_KERNEL_FOURIER) : opt.separable;
+    if (h->separable && kernel->kind != TB_KERNEL_FOURIER) {
+        delete h;
+        return fail(TB_EINVAL, "separable factors need a kernel that is a product over modes (FOURIER)");
+    }
+    h->precisions = opt.precisions ? opt.precisions : TB_PRECISIONS_BUILT;
+    if (h->precisions & ~TB_PRECISIONS_BUILT) {
+        delete h;
+        return fail(TB_EUNSUPPORTED, "requested apply precision is not built into this library");
+    }
+    h->use_graphs = opt.use_graphs;
+    h->proxy_rows = opt.proxy_rows;
+    h->rank_max = opt.rank_max;
+    h->seed = opt.seed;
+    h->rank_min = 1 << 30;
+    h->ks.kind = kernel->kind;
+    for (int i = 0; i < 4; ++i) h->ks.p[i] = kernel->params[i];
+    if (kernel->kind == TB_KERNEL_HELMHOLTZ) h->ks.p[1] = kernel->params[0] / (2.0 * M_PI);
+    for (int k = 0; k < d; ++k) {
+        h->n[k] = n[k];
+        h->cb[k] = n[k] >> L;
+    }
+    tb_status st = build_impl(h, grids);
+    if (st != TB_OK) {
+        std::string msg = g_err;
+        tb_free(h);
+        g_err = msg;
+        return st;
+    }
+    h->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = h;
+    return TB_OK;
+}
+
+extern "C" tb_status tb_query(tb_handle h, tb_info *info) {
+    if (!h || !info) return fail(TB_EINVAL, "handle and info must be non-NULL");
+    std::memset(info, 0, sizeof(*info));
+    info->d = h->d;
+    info->L = h->L;
+    info->Lc = h->Lc;
+    info->order = h->order;
+    info->separable = h->separable;
+    for (int k = 0; k < h->d; ++k) {
+        info->n[k] = h->n[k];
+        info->cb[k] = h->cb[k];
+    }
+    int64_t fe = 0;
+    for (int l = 0; l <= h->Lc; ++l)
+        for (int k = 0; k < h->d; ++k) {
+            info->rank_src[l][k] = h->src[l].R[k];
+            info->rank_tgt[l][k] = h->tgt[l].R[k];
+            fe += h->src[l].count[k] * h->src[l].R[k] * h->src[l].cin[k];
+            fe += h->tgt[l].count[k] * h->tgt[l].R[k] * h->tgt[l].cin[k];
+        }
+    info->rank_min = h->rank_min;
+    info->rank_max = h->rank_max_seen;
+    info->num_ids = h->num_ids;
+    info->core_entries = h->core_entries;
+    info->factor_entries = fe;
+    info->level_entries_max = h->level_max;
+    info->device_bytes = h->device_bytes + (int64_t)h->ws.bytes * 2;
+    info->build_seconds = h->build_seconds;
+    return TB_OK;
+}
+
+// --------------------------------------------------------------------- apply
+namespace {
+
+template <class R>
+TileBuf<R> tilebuf(const tb_plan *h, int side, int l, void *p) {
+    const SideLevel &S = side == 0 ? h->src[l] : h->tgt[l];
+    TileBuf<R> t;
+    t.p = static_cast<cx<R> *>(p);
+    t.tsize = 1;
+    for (int k = 0; k < TB_MAX_D; ++k) t.R[k] = k < h->d ? S.R[k] : 1;
+    for (int k = 0; k < h->d; ++k) t.tsize *= S.R[k];
+    t.lgseg = h->Lc - l;
+    t.nM = ipow2(h->d * l);
+    t.layout = side;
+    return t;
+}
+
+template <class R>
+const cx<R> *facptr(const SideLevel &S, int k);
+template <>
+const cx<double> *facptr<double>(const SideLevel &S, int k) { return S.fac64[k]; }
+template <>
+const cx<float> *facptr<float>(const SideLevel &S, int k) { return S.fac32[k]; }
+
+template <class R>
+FacRef<R> facref(const tb_plan *h, int side, int l) {
+    const SideLevel &S = side == 0 ? h->src[l] : h->tgt[l];
+    FacRef<R> f;
+    std::memset(&f, 0, sizeof(f));
+    for (int k = 0; k < h->d; ++k) {
+        f.A[k] = facptr<R>(S, k);
+        f.rows[k] = S.R[k];
+        f.cols[k] = S.cin[k];
+    }
+    f.l = l;
+    f.lgseg = h->Lc - l;
+    f.nM = ipow2(h->d * l);
+    f.separable = h->separable;
+    return f;
+}
+
+// Largest RHS chunk whose shared-memory plan fits `limit` bytes (at least 1).
+template <class R>
+tb_status pick_chunk(int d, const int *m, const int *o, int64_t nv, int64_t &nvc, size_t &smem, int &offX,
+                     int &offB0, int &offB1, int &offY, int &offA, bool no_x = false, bool no_y = false) {
+    auto plan = [&](int64_t c) {
+        ChainSmem s = chain_smem(d, m, o, c);
+        if (no_x) s.x = 0;   // the first pass reads global memory directly
+        if (no_y) s.y = 0;   // the last pass writes global memory directly
+        return s;
+    };
+    ChainSmem s1 = plan(1);
+    const int64_t per = s1.x + s1.b0 + s1.b1 + s1.y;
+    const int64_t es = sizeof(cx<R>);
+    const int64_t limit = 100 * 1024;
+    int64_t c = (limit / es - s1.a) / std::max<int64_t>(per, 1);
+    if (c < 1) c = 1;
+    if (c > nv) c = nv;
+    nvc = c;
+    ChainSmem s = plan(nvc);
+    offX = 0;
+    offB0 = (int)s.x;
+    offB1 = (int)(s.x + s.b0);
+    offY = (int)(s.x + s.b0 + s.b1);
+    offA = (int)(s.x + s.b0 + s.b1 + s.y);
+    smem = (size_t)(s.x + s.b0 + s.b1 + s.y + s.a) * es;
+    if (smem > g_smem_optin)
+        return fail(TB_EUNSUPPORTED, "tile of " + std::to_string(smem) + " bytes exceeds shared memory (" +
+                                         std::to_string(g_smem_optin) + ")");
+    return TB_OK;
+}
+
+template <class R>
+tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out, int64_t nv,
+                     cudaStream_t st) {
+    const int d = h->d, Lc = h->Lc;
+    LevelArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.d = d;
+    a.Lc = Lc;
+    a.nF = ipow2(d * Lc);
+    a.nv = nv;
+    int m[TB_MAX_D], o[TB_MAX_D];
+    const SideLevel *S = side == 0 ? h->src : h->tgt;
+    for (int k = 0; k < d; ++k) {
+        a.cb[k] = (int)h->cb[k];
+        a.nmid[k] = h->n[k] >> Lc;
+        a.perm[k] = h->perm[k];
+    }
+    int64_t gs = 1;
+    for (int k = d - 1; k >= 0; --k) {
+        a.user.gstride[k] = gs;
+        gs *= h->n[k];
+    }
+    switch (pass) {
+        case Pass::LeafIn:
+            a.user.p = (cx<R> *)in;
+            a.out = tilebuf<R>(h, side, 0, out);
+            a.fac = facref<R>(h, side, 0);
+            for (int k = 0; k < d; ++k) { m[k] = (int)h->cb[k]; o[k] = S[0].R[k]; }
+            a.nblocks = a.nF << (Lc * d);
+            break;
+        case Pass::LeafOut:
+            a.user.p = (cx<R> *)out;
+            a.in = tilebuf<R>(h, side, 0, (void *)in);
+            a.fac = facref<R>(h, side, 0);
+            for (int k = 0; k < d; ++k) { m[k] = S[0].R[k]; o[k] = (int)h->cb[k]; }
+            a.nblocks = a.nF << (Lc * d);
+            break;
+        case Pass::Split:
+            a.in = tilebuf<R>(h, side, l - 1, (void *)in);
+            a.out = tilebuf<R>(h, side, l, out);
+            a.fac = facref<R>(h, side, l);
+            for (int k = 0; k < d; ++k) { m[k] = 2 * S[l - 1].R[k]; o[k] = S[l].R[k]; }
+            a.nblocks = h->P >> d;
+            break;
+        case Pass::Gather:
+            a.in = tilebuf<R>(h, side, l, (void *)in);
+            a.out = tilebuf<R>(h, side, l - 1, out);
+            a.fac = facref<R>(h, side, l);
+            for (int k = 0; k < d; ++k) { m[k] = S[l].R[k]; o[k] = 2 * S[l - 1].R[k]; }
+            a.nblocks = h->P >> d;
+            break;
+    }
+    TB_TRY(pick_chunk<R>(d, m, o, nv, a.nvc, a.smem, a.offX, a.offB0, a.offB1, a.offY, a.offA,
+                         pass == Pass::LeafIn, pass == Pass::LeafOut));
+    TB_CK(launch_level<R>(pass, conj, a, st));
+    return TB_OK;
+}
+
+template <class R>
+const cx<R> *coreptr(const tb_plan *h);
+template <>
+const cx<double> *coreptr<double>(const tb_plan *h) { return h->core64; }
+template <>
+const cx<float> *coreptr<float>(const tb_plan *h) { return h->core32; }
+
+template <class R>
+tb_status core_pass(const tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st) {
+    const int d = h->d, Lc = h->Lc;
+    CoreApplyArgs<R> a;
+    std::memset(&a, 0, sizeof(a));
+    a.d = d;
+    a.P = h->P;
+    a.nv = nv;
+    a.Lc = Lc;
+    a.in = tilebuf<R>(h, adjoint ? 1 : 0, Lc, (void *)in);
+    a.out = tilebuf<R>(h, adjoint ? 0 : 1, Lc, out);
+    const int64_t es = sizeof(cx<R>);
+    if (h->separable) {
+        int m[TB_MAX_D], o[TB_MAX_D];
+        for (int k = 0; k < d; ++k) {
+            a.Rt[k] = h->tgt[Lc].R[k];
+            a.Rs[k] = h->src[Lc].R[k];
+            a.kron[k] = std::is_same<R, double>::value ? (const cx<R> *)h->kron64[k] : (const cx<R> *)h->kron32[k];
+            m[k] = adjoint ? a.Rt[k] : a.Rs[k];
+            o[k] = adjoint ? a.Rs[k] : a.Rt[k];
+        }
+        TB_TRY(pick_chunk<R>(d, m, o, nv, a.nvc, a.smem, a.offX, a.offB0, a.offB1, a.offY, a.offA));
+        TB_CK(launch_core_kron<R>(adjoint, a, st));
+        return TB_OK;
+    }
+    a.dims = h->core_dims;
+    a.off = h->core_off;
+    a.core = coreptr<R>(h);
+    const int64_t tmax = std::max(prod_tile(h->src[Lc], d), prod_tile(h->tgt[Lc], d));
+    int64_t c = (96 * 1024) / (tmax * es);
+    c = std::max<int64_t>(1, std::min<int64_t>({c, nv, 16}));
+    a.nvc = c;
+    a.smem = (size_t)(tmax * c * es);
+    if (a.smem > g_smem_optin) return fail(TB_EUNSUPPORTED, "core block exceeds shared memory");
+    TB_CK(launch_core_dense<R>(adjoint, a, st));
+    return TB_OK;
+}
+
+// Real flops of one mode-product chain X (dims m) -> Y (dims o), per RHS.
+double chain_flops(int d, const int *m, const int *o) {
+    double f = 0.0;
+    for (int k = 0; k < d; ++k) {
+        double t = (double)m[k] * o[k];
+        for (int i = 0; i < k; ++i) t *= o[i];
+        for (int i = k + 1; i < d; ++i) t *= m[i];
+        f += 8.0 * t;
+    }
+    return f;
+}
+
+// Bytes and flops one launch of a pass must move / execute (stored sizes).
+void pass_cost(const tb_plan *h, Pass pass, int side, int l, int64_t nv, size_t es, int64_t &bytes, double &flops) {
+    const int d = h->d;
+    const SideLevel *S = side == 0 ? h->src : h->tgt;
+    int64_t N = 1;
+    for (int k = 0; k < d; ++k) N *= h->n[k];
+    auto tensor = [&](int lv) { return h->P * prod_tile(S[lv], d) * nv * (int64_t)es; };
+    auto facb = [&](int lv) {
+        int64_t b = 0;
+        for (int k = 0; k < d; ++k) b += S[lv].count[k] * S[lv].R[k] * S[lv].cin[k];
+        return b * (int64_t)es;
+    };
+    int m[TB_MAX_D], o[TB_MAX_D];
+    switch (pass) {
+        case Pass::LeafIn:
+        case Pass::LeafOut:
+            bytes = N * nv * (int64_t)es + tensor(0) + facb(0);
+            for (int k = 0; k < d; ++k) { m[k] = (int)h->cb[k]; o[k] = S[0].R[k]; }
+            if (pass == Pass::LeafOut) std::swap(m, o);
+            flops = (double)h->P * nv * chain_flops(d, m, o);
+            break;
+        case Pass::Split:
+        case Pass::Gather:
+            bytes = tensor(l - 1) + tensor(l) + facb(l);
+            for (int k = 0; k < d; ++k) { m[k] = 2 * S[l - 1].R[k]; o[k] = S[l].R[k]; }
+            if (pass == Pass::Gather) std::swap(m, o);
+            flops = (double)h->P * nv * chain_flops(d, m, o);
+            break;
+    }
+}
+
+template <class R>
+tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st, bool prof) {
+    void *B[2] = {h->ws.buf[0], h->ws.buf[1]};
+    const int Lc = h->Lc, d = h->d;
+    const int first = adjoint ? 1 : 0, second = 1 - first;   // side traversed first / last
+    const size_t es = sizeof(cx<R>);
+    auto timed = [&](const char *name, int level, int64_t bytes, double flops, auto &&fn) -> tb_status {
+        ProfRec r{name, level, (int)adjoint, nullptr, nullptr, bytes, flops};
+        if (prof) {
+            TB_CK(cudaEventCreate(&r.e0));
+            TB_CK(cudaEventCreate(&r.e1));
+            TB_CK(cudaEventRecord(r.e0, st));
+        }
+        tb_status s = fn();
+        if (prof) {
+            TB_CK(cudaEventRecord(r.e1, st));
+            h->prof.push_back(r);
+        }
+        return s;
+    };
+    auto level = [&](Pass p, const char *name, int side, int l, const void *i, void *o) -> tb_status {
+        int64_t bytes = 0;
+        double flops = 0;
+        if (prof) pass_cost(h, p, side, l, nv, es, bytes, flops);
+        return timed(name, l, bytes, flops, [&] { return level_pass<R>(h, p, adjoint, side, l, i, o, nv, st); });
+    };
+    int cur = 0;
+    TB_TRY(level(Pass::LeafIn, "leaf_in", first, 0, in, B[cur]));
+    for (int l = 1; l <= Lc; ++l) {
+        TB_TRY(level(Pass::Split, "split", first, l, B[cur], B[cur ^ 1]));
+        cur ^= 1;
+    }
+    {
+        int64_t bytes = 0;
+        double flops = 0;
+        if (prof) {
+            if (h->separable) {
+                int m[TB_MAX_D], o[TB_MAX_D];
+                int64_t kb = 0;
+                for (int k = 0; k < d; ++k) {
+                    m[k] = h->src[Lc].R[k];
+                    o[k] = h->tgt[Lc].R[k];
+                    kb += (int64_t)(1 << Lc) * (1 << Lc) * m[k] * o[k];
+                }
+                bytes = (h->P * (prod_tile(h->src[Lc], d) + prod_tile(h->tgt[Lc], d)) * nv + kb) * (int64_t)es;
+                flops = (double)h->P * nv * chain_flops(d, m, o);
+            } else {
+                bytes = (h->core_entries + (h->core_in_entries + h->core_out_entries) * nv) * (int64_t)es;
+                flops = 8.0 * (double)h->core_entries * nv;
+            }
+        }
+        TB_TRY(timed("core", Lc, bytes, flops, [&] { return core_pass<R>(h, adjoint, B[cur], B[cur ^ 1], nv, st); }));
+        cur ^= 1;
+    }
+    for (int l = Lc; l >= 1; --l) {
+        TB_TRY(level(Pass::Gather, "gather", second, l, B[cur], B[cur ^ 1]));
+        cur ^= 1;
+    }
+    TB_TRY(level(Pass::LeafOut, "leaf_out", second, 0, B[cur], out));
+    return TB_OK;
+}
+
+tb_status ensure_workspace(tb_plan *h, int64_t nv) {
+    const size_t need = (size_t)h->level_max * (size_t)nv * sizeof(c128);
+    if (need <= h->ws.bytes) return TB_OK;
+    TB_CK(cudaDeviceSynchronize());
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+    for (int i = 0; i < 2; ++i) {
+        if (h->ws.buf[i]) cudaFree(h->ws.buf[i]);
+        h->ws.buf[i] = nullptr;
+    }
+    h->ws.bytes = 0;
+    for (int i = 0; i < 2; ++i) TB_CK(cudaMalloc(&h->ws.buf[i], need));
+    for (int i = 0; i < 2; ++i) TB_CK(cudaMemset(h->ws.buf[i], 0, need));
+    h->ws.bytes = need;
+    return TB_OK;
+}
+
+tb_status apply_common(tb_handle h, const void *in, void *out, int64_t nv, int precision, void *stream,
+                       bool adjoint) {
+    if (!h) return fail(TB_EINVAL, "handle is NULL");
+    if (nv <= 0) return fail(TB_EINVAL, "nv must be positive");
+    if (precision < TB_PREC_C128 || precision > TB_PREC_C64_SPLITBF16)
+        return fail(TB_EINVAL, "unknown precision");
+    if (!(h->precisions & (1u << precision)))
+        return fail(TB_EUNSUPPORTED, "handle was built without precision " + std::to_string(precision));
+    TB_TRY(check_device_ptr(in, adjoint ? "g" : "f"));
+    TB_TRY(check_device_ptr(out, adjoint ? "v" : "u"));
+    int64_t N = 1;
+    for (int k = 0; k < h->d; ++k) N *= h->n[k];
+    const size_t es = precision == TB_PREC_C128 ? 16 : 8;
+    const char *a0 = (const char *)in, *b0 = (const char *)out;
+    const size_t bytes = (size_t)N * nv * es;
+    if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(TB_EINVAL, "input and output overlap");
+    if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
+    if (g_smem_optin == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+        g_smem_optin = (size_t)v;
+    }
+    TB_TRY(ensure_workspace(h, nv));
+    cudaStream_t st = (cudaStream_t)stream;
+    auto launch_all = [&](bool prof) -> tb_status {
+        if (precision == TB_PREC_C128) return run_chain<double>(h, adjoint, in, out, nv, st, prof);
+        return run_chain<float>(h, adjoint, in, out, nv, st, prof);
+    };
+    const bool prof = h->profiling != 0;
+    if (!h->use_graphs || st == nullptr) return launch_all(prof);
+    for (auto &g : h->graphs)
+        if (g.in == in && g.out == out && g.nv == nv && g.prec == precision && g.adjoint == (int)adjoint &&
+            g.stream == st) {
+            TB_CK(cudaGraphLaunch(g.exec, st));
+            return TB_OK;
+        }
+    // first call for these arguments: run eagerly once (sets kernel attributes), then capture
+    TB_TRY(launch_all(prof));
+    cudaGraph_t graph;
+    TB_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    tb_status s = launch_all(false);
+    cudaError_t e = cudaStreamEndCapture(st, &graph);
+    if (s != TB_OK) return s;
+    if (e != cudaSuccess) return fail(TB_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(TB_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    h->graphs.push_back(GraphEntry{in, out, nv, precision, (int)adjoint, st, exec});
+    return TB_OK;
+}
+
+}  // namespace
+
+extern "C" tb_status tb_apply(tb_handle h, const void *f, void *u, int64_t nv, int precision, void *stream) {
+    return apply_common(h, f, u, nv, precision, stream, false);
+}
+
+extern "C" tb_status tb_apply_adjoint(tb_handle h, const void *g, void *v, int64_t nv, int precision, void *stream) {
+    return apply_common(h, g, v, nv, precision, stream, true);
+}
+
+extern "C" tb_status tb_apply_host(tb_handle h, const void *f, void *u, int64_t nv, int precision) {
+    if (!h || !f || !u) return fail(TB_EINVAL, "handle, f and u must be non-NULL");
+    if (nv <= 0) return fail(TB_EINVAL, "nv must be positive");
+    int64_t N = 1;
+    for (int k = 0; k < h->d; ++k) N *= h->n[k];
+    const size_t es = precision == TB_PREC_C128 ? 16 : 8;
+    const size_t bytes = (size_t)N * nv * es;
+    if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
+    if (bytes > h->ws.host_bytes) {
+        TB_CK(cudaDeviceSynchronize());
+        if (h->ws.host_in) cudaFree(h->ws.host_in);
+        if (h->ws.host_out) cudaFree(h->ws.host_out);
+        h->ws.host_in = h->ws.host_out = nullptr;
+        h->ws.host_bytes = 0;
+        TB_CK(cudaMalloc(&h->ws.host_in, bytes));
+        TB_CK(cudaMalloc(&h->ws.host_out, bytes));
+        h->ws.host_bytes = bytes;
+    }
+    TB_CK(cudaMemcpy(h->ws.host_in, f, bytes, cudaMemcpyHostToDevice));
+    TB_TRY(apply_common(h, h->ws.host_in, h->ws.host_out, nv, precision, nullptr, false));
+    TB_CK(cudaMemcpy(u, h->ws.host_out, bytes, cudaMemcpyDeviceToHost));
+    return TB_OK;
+}
+
+extern "C" tb_status tb_profile_enable(tb_handle h, int on) {
+    if (!h) return fail(TB_EINVAL, "handle is NULL");
+    h->profiling = on ? 1 : 0;
+    return TB_OK;
+}
+
+extern "C" tb_status tb_profile_stats(tb_handle h, tb_pass_stat *stats, int cap, int *count) {
+    if (!h || !count || (cap > 0 && !stats)) return fail(TB_EINVAL, "handle, stats and count must be non-NULL");
+    std::vector<tb_pass_stat> agg;
+    tb_status st = TB_OK;
+    for (auto &r : h->prof) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.e0, r.e1);
+        if (e != cudaSuccess && st == TB_OK) st = fail(TB_ECUDA, std::string("profile events: ") + cudaGetErrorString(e));
+        cudaEventDestroy(r.e0);
+        cudaEventDestroy(r.e1);
+        tb_pass_stat *hit = nullptr;
+        for (auto &a : agg)
+            if (!std::strcmp(a.name, r.name) && a.level == r.level && a.adjoint == r.adjoint) hit = &a;
+        if (!hit) {
+            tb_pass_stat z;
+            std::memset(&z, 0, sizeof(z));
+            std::snprintf(z.name, sizeof(z.name), "%s", r.name);
+            z.level = r.level;
+            z.adjoint = r.adjoint;
+            agg.push_back(z);
+            hit = &agg.back();
+        }
+        hit->launches += 1;
+        hit->ms_total += ms;
+        hit->bytes = r.bytes;
+        hit->flops = r.flops;
+    }
+    h->prof.clear();
+    *count = (int)std::min<size_t>(agg.size(), (size_t)std::max(cap, 0));
+    for (int i = 0; i < *count; ++i) stats[i] = agg[(size_t)i];
+    return st;
+}

@@ -1,0 +1,99 @@
+// Host-side plan of a built tensor butterfly and the device-side views that the
+// construction and apply kernels receive by value.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "tb_common.cuh"
+
+namespace tb {
+
+// Interpolation / transfer factors of one side at one level (Alg. 1 output):
+// for each mode k, `count[k]` blocks of R[k] x cin[k] entries, row-major.
+// Rows are the skeleton entries of the block in pivot order (zero rows pad up
+// to R[k]); columns are the candidate entries: the C_b leaf points at level 0,
+// or the two child skeletons (child 1 in [0, R_{l-1,k}), child 2 in
+// [R_{l-1,k}, 2 R_{l-1,k})) at level l > 0, zero-padded.
+struct SideLevel {
+    int R[MAXD] = {0};
+    int cin[MAXD] = {0};
+    int cap[MAXD] = {0};       // skeleton slots per block during construction
+    int64_t count[MAXD] = {0};
+    c128 *fac64[MAXD] = {nullptr};
+    c64 *fac32[MAXD] = {nullptr};
+    int *skel[MAXD] = {nullptr};   // count x cap grid indices (-1 = none)
+    int *rank[MAXD] = {nullptr};   // count
+    int rmin = 0, rmax = 0;
+};
+
+struct Workspace {
+    void *buf[2] = {nullptr, nullptr};
+    size_t bytes = 0;          // per buffer
+    void *host_in = nullptr;   // device staging for tb_apply_host
+    void *host_out = nullptr;
+    size_t host_bytes = 0;
+};
+
+struct ProfRec {
+    const char *name;
+    int level, adjoint;
+    cudaEvent_t e0, e1;
+    int64_t bytes;
+    double flops;
+};
+
+struct GraphEntry {
+    const void *in;
+    void *out;
+    int64_t nv;
+    int prec;
+    int adjoint;
+    cudaStream_t stream;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace tb
+
+struct tb_plan {
+    int d = 0, L = 0, Lc = 0, order = 0, separable = 0, device = 0;
+    int64_t n[TB_MAX_D] = {0}, cb[TB_MAX_D] = {0};
+    double tol = 0;
+    unsigned precisions = 0;
+    int use_graphs = 0;
+    tb::KernelSpec ks{};
+    int proxy_rows = 1024, rank_max = 32;
+    uint64_t seed = 0;
+
+    // grids and per-axis tree orderings (tree position -> grid index), device
+    double *xs[TB_MAX_D] = {nullptr}, *ys[TB_MAX_D] = {nullptr};
+    int *perm[TB_MAX_D] = {nullptr};
+
+    tb::SideLevel src[TB_MAX_LEVELS], tgt[TB_MAX_LEVELS];
+
+    // mid-level cores K(t-bar, s-bar): P pairs, compact storage
+    int64_t P = 0;
+    int64_t *core_off = nullptr;   // P + 1 offsets into the core arrays (device)
+    int *core_dims = nullptr;      // P x 2d: target ranks then source ranks (device)
+    tb::c128 *core64 = nullptr;
+    tb::c64 *core32 = nullptr;
+    tb::c64 *core_bf = nullptr;    // split-BF16 storage (hi, lo) reinterpreted, see tb_core_tc.cu
+    int64_t core_entries = 0;
+    int64_t core_in_entries = 0;   // sum over pairs of prod_k |s-bar_k| (compact core columns)
+    int64_t core_out_entries = 0;  // sum over pairs of prod_k |t-bar_k|
+    int profiling = 0;
+    std::vector<tb::ProfRec> prof;
+    // separable (Kronecker) cores: per mode k, (2^Lc x 2^Lc) blocks of Rt x Rs
+    tb::c128 *kron64[TB_MAX_D] = {nullptr};
+    tb::c64 *kron32[TB_MAX_D] = {nullptr};
+
+    int64_t level_max = 0;         // largest level tensor, entries per RHS
+    tb::Workspace ws;
+    std::vector<tb::GraphEntry> graphs;
+    std::vector<void *> allocations;
+    int64_t device_bytes = 0;
+    int64_t num_ids = 0;
+    int rank_min = 0, rank_max_seen = 0;
+    double build_seconds = 0;
+    int *d_err = nullptr;          // device error word of the construction kernels
+};

@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads and exports every symbol of include/tb.h, and
+argument checks that need no GPU reject bad input (no GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2411_03029_gb300 as tb
+from paper_2411_03029_gb300 import build as tbbuild
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "tb.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[a-z_]+\s*\*?\s*(tb_[a-z_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    tbbuild.build()
+    return tb.lib()
+
+
+def test_header_declares_the_abi():
+    names = declared_functions()
+    for must in ("tb_build", "tb_apply", "tb_apply_adjoint", "tb_free"):
+        assert must in names
+    assert set(names) == set(tb.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_version_and_defaults(lib):
+    assert b"sm_103a" in lib.tb_version()
+    opt = tb._Options()
+    assert lib.tb_options_default(ctypes.byref(opt)) == 0
+    assert opt.L == -1 and opt.proxy_rows == 1024 and opt.rank_max == 32 and opt.separable == -1
+
+
+def test_free_null_is_ok(lib):
+    assert lib.tb_free(None) == 0
+
+
+def test_build_rejects_bad_arguments_without_touching_the_gpu(lib):
+    kern = tb._Kernel(tb.KERNEL_FOURIER, (ctypes.c_double * 4)())
+    grids = tb._Grids()
+    h = ctypes.c_void_p()
+    n = (ctypes.c_int64 * 2)(16, 16)
+    # d out of range
+    assert lib.tb_build(ctypes.byref(kern), 0, ctypes.cast(n, ctypes.c_void_p), ctypes.byref(grids), 1e-6,
+                        ctypes.byref(h)) == 1
+    assert b"d must be" in lib.tb_last_error()
+    # NULL grid pointers
+    assert lib.tb_build(ctypes.byref(kern), 2, ctypes.cast(n, ctypes.c_void_p), ctypes.byref(grids), 1e-6,
+                        ctypes.byref(h)) == 1
+    # tolerance
+    assert lib.tb_build(ctypes.byref(kern), 2, ctypes.cast(n, ctypes.c_void_p), ctypes.byref(grids), 2.0,
+                        ctypes.byref(h)) == 1
+    # bad kernel kind
+    bad = tb._Kernel(9, (ctypes.c_double * 4)())
+    assert lib.tb_build(ctypes.byref(bad), 2, ctypes.cast(n, ctypes.c_void_p), ctypes.byref(grids), 1e-6,
+                        ctypes.byref(h)) == 1
+    assert not h.value
+
+
+def test_apply_rejects_null_handle(lib):
+    assert lib.tb_apply(None, None, None, 1, 0, None) == 1
+    assert lib.tb_apply_adjoint(None, None, None, 1, 0, None) == 1
+    assert lib.tb_query(None, None) == 1

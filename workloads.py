@@ -65,29 +65,29 @@ WORKLOADS = {
     # d=2 uniform DFT, 64 points per direction, FP64 build and apply (Sec. 4.3 kernel).
     "fourier2d_n64": _wl(
         name="fourier2d_n64", kind=FOURIER, d=2, n=64, tol=1e-8, nv=1, precision=C128,
-        bound=1e-7, rhs_seeds=(0,), samples=0, order=ORDER_BITREV,
+        bound=1e-7, rhs_seeds=(0,), samples=0, order=ORDER_BITREV, L=4,
         description="d=2 Fourier exp(-2 pi i x.y), x=i/n, y=j-n/2, n=64, FP64"),
     # Green's function between [0,1)^3 and [2,3)x[0,1)^2, 16 wavelengths (Sec. 4.1 geometry).
     "helmholtz3d_n64": _wl(
         name="helmholtz3d_n64", kind=HELMHOLTZ, d=3, n=64, tol=1e-6, nv=1, precision=C64,
         bound=1e-5, params=(2 * math.pi * 16,), rhs_seeds=(0,), samples=4096,
-        src_offset=(2.0, 0.0, 0.0),
+        src_offset=(2.0, 0.0, 0.0), L=4,
         description="d=3 Helmholtz exp(i k r)/r, cubes 2 apart on axis 1, n=64, k=2 pi 16, c64"),
     # Same geometry at 64 wavelengths, 16 right-hand sides, split-BF16 core contraction.
     "helmholtz3d_n256": _wl(
         name="helmholtz3d_n256", kind=HELMHOLTZ, d=3, n=256, tol=1e-4, nv=16,
         precision=C64_SPLITBF16, bound=1e-3, params=(2 * math.pi * 64,),
-        rhs_seeds=tuple(range(16)), samples=4096, src_offset=(2.0, 0.0, 0.0),
+        rhs_seeds=tuple(range(16)), samples=4096, src_offset=(2.0, 0.0, 0.0), L=4,
         description="d=3 Helmholtz, n=256, k=2 pi 64, 16 RHS, split BF16"),
     # 2-D generalized Radon transform with c(x) = (2 + sin(2 pi x1) sin(2 pi x2)) / 16.
     "radon2d_n256": _wl(
         name="radon2d_n256", kind=RADON, d=2, n=256, tol=1e-6, nv=1, precision=C64,
-        bound=1e-4, params=(2.0 / 16.0, 1.0 / 16.0), rhs_seeds=(1,), samples=4096,
+        bound=1e-4, params=(2.0 / 16.0, 1.0 / 16.0), rhs_seeds=(1,), samples=4096, L=6,
         description="d=2 Radon exp(2 pi i (x.xi + c(x)|xi|)), n=256, c64, autograd"),
     # d=6 uniform DFT, 16 points per direction, 8 right-hand sides.
     "fourier6d_n16": _wl(
         name="fourier6d_n16", kind=FOURIER, d=6, n=16, tol=1e-6, nv=8, precision=C64,
-        bound=1e-5, rhs_seeds=tuple(range(8)), samples=4096, order=ORDER_BITREV,
+        bound=1e-5, rhs_seeds=tuple(range(8)), samples=4096, order=ORDER_BITREV, L=2,
         description="d=6 Fourier, n=16, 8 RHS, c64"),
 }
 
