@@ -16,7 +16,8 @@ using namespace tb;
 static thread_local std::string g_err;
 
 // apply precisions this library implements (bit i = tb_precision i)
-static const unsigned TB_PRECISIONS_BUILT = (1u << TB_PREC_C128) | (1u << TB_PREC_C64);
+static const unsigned TB_PRECISIONS_BUILT =
+    (1u << TB_PREC_C128) | (1u << TB_PREC_C64) | (1u << TB_PREC_C64_SPLITBF16);
 
 static tb_status fail(tb_status s, const std::string &msg) {
     g_err = msg;
@@ -309,6 +310,47 @@ static tb_status build_cores(tb_plan *h) {
     a.out32 = h->core32;
     TB_CK(launch_core_eval(a, 0));
     TB_CK(cudaDeviceSynchronize());
+    if (h->precisions & (1u << TB_PREC_C64_SPLITBF16)) {
+        // split-BF16 tiles of K(t-bar, s-bar) and of its conjugate transpose
+        const int NTc = core_tc_rows_per_item(), KCc = core_tc_cols_per_chunk();
+        for (int dir = 0; dir < 2; ++dir) {
+            std::vector<CoreItem> items;
+            int64_t boff = 0;
+            for (int64_t p = 0; p < h->P; ++p) {
+                int64_t mt = 1, ms = 1;
+                for (int k = 0; k < d; ++k) {
+                    mt *= dims[(size_t)p * 2 * d + k];
+                    ms *= dims[(size_t)p * 2 * d + d + k];
+                }
+                const int64_t nrows = dir ? ms : mt, ncols = dir ? mt : ms;
+                const int64_t np = (nrows + 15) / 16 * 16;
+                const int nkc = (int)((ncols + KCc - 1) / KCc);
+                for (int64_t j = 0; j * NTc < np; ++j) {
+                    const int rows = (int)std::min<int64_t>(NTc, np - j * NTc);
+                    items.push_back(CoreItem{(int)p, (int)j, rows, nkc, boff});
+                    boff += (int64_t)nkc * rows * 256;
+                }
+            }
+            h->tc_nitems[dir] = (int64_t)items.size();
+            h->tc_bytes[dir] = boff;
+            TB_TRY(dalloc(h, &h->tc_items[dir], (int64_t)items.size()));
+            TB_CK(cudaMemcpy(h->tc_items[dir], items.data(), items.size() * sizeof(CoreItem), cudaMemcpyHostToDevice));
+            TB_TRY(dalloc(h, &h->tc_tiles[dir], boff));
+            CoreTileArgs ta;
+            std::memset(&ta, 0, sizeof(ta));
+            ta.d = d;
+            ta.adjoint = dir;
+            ta.nitems = h->tc_nitems[dir];
+            ta.items = h->tc_items[dir];
+            ta.dims = h->core_dims;
+            ta.core_off = h->core_off;
+            ta.c128 = h->core64;
+            ta.c64 = h->core32;
+            ta.out = h->tc_tiles[dir];
+            TB_CK(launch_core_tile(ta, 0));
+        }
+        TB_CK(cudaDeviceSynchronize());
+    }
     return TB_OK;
 }
 
@@ -630,9 +672,43 @@ const cx<double> *coreptr<double>(const tb_plan *h) { return h->core64; }
 template <>
 const cx<float> *coreptr<float>(const tb_plan *h) { return h->core32; }
 
-template <class R>
-tb_status core_pass(const tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st) {
+// Split-BF16 tensor-core core contraction (complex64 tiles), 16 RHS per launch.
+tb_status core_pass_tc(const tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st) {
     const int d = h->d, Lc = h->Lc;
+    const int dir = adjoint ? 1 : 0;
+    const TileBuf<float> tin = tilebuf<float>(h, adjoint ? 1 : 0, Lc, (void *)in);
+    const TileBuf<float> tout = tilebuf<float>(h, adjoint ? 0 : 1, Lc, out);
+    CoreTcArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.d = d;
+    a.adjoint = dir;
+    a.nitems = h->tc_nitems[dir];
+    a.items = h->tc_items[dir];
+    a.tiles = h->tc_tiles[dir];
+    a.dims = h->core_dims;
+    a.in = tin.p;
+    a.out = tout.p;
+    a.in_tsize = tin.tsize;
+    a.out_tsize = tout.tsize;
+    for (int k = 0; k < d; ++k) {
+        a.in_R[k] = tin.R[k];
+        a.out_R[k] = tout.R[k];
+    }
+    a.nv = (int)nv;
+    a.err = h->d_err;
+    for (int64_t v0 = 0; v0 < nv; v0 += 16) {
+        a.v0 = (int)v0;
+        a.nvc = (int)std::min<int64_t>(16, nv - v0);
+        TB_CK(launch_core_tc(a, st));
+    }
+    return TB_OK;
+}
+
+template <class R>
+tb_status core_pass(const tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st,
+                    int precision) {
+    const int d = h->d, Lc = h->Lc;
+    if (precision == TB_PREC_C64_SPLITBF16 && !h->separable) return core_pass_tc(h, adjoint, in, out, nv, st);
     CoreApplyArgs<R> a;
     std::memset(&a, 0, sizeof(a));
     a.d = d;
@@ -712,7 +788,8 @@ void pass_cost(const tb_plan *h, Pass pass, int side, int l, int64_t nv, size_t 
 }
 
 template <class R>
-tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st, bool prof) {
+tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st, bool prof,
+                    int precision) {
     void *B[2] = {h->ws.buf[0], h->ws.buf[1]};
     const int Lc = h->Lc, d = h->d;
     const int first = adjoint ? 1 : 0, second = 1 - first;   // side traversed first / last
@@ -762,7 +839,8 @@ tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t
                 flops = 8.0 * (double)h->core_entries * nv;
             }
         }
-        TB_TRY(timed("core", Lc, bytes, flops, [&] { return core_pass<R>(h, adjoint, B[cur], B[cur ^ 1], nv, st); }));
+        TB_TRY(timed("core", Lc, bytes, flops,
+                     [&] { return core_pass<R>(h, adjoint, B[cur], B[cur ^ 1], nv, st, precision); }));
         cur ^= 1;
     }
     for (int l = Lc; l >= 1; --l) {
@@ -815,8 +893,8 @@ tb_status apply_common(tb_handle h, const void *in, void *out, int64_t nv, int p
     TB_TRY(ensure_workspace(h, nv));
     cudaStream_t st = (cudaStream_t)stream;
     auto launch_all = [&](bool prof) -> tb_status {
-        if (precision == TB_PREC_C128) return run_chain<double>(h, adjoint, in, out, nv, st, prof);
-        return run_chain<float>(h, adjoint, in, out, nv, st, prof);
+        if (precision == TB_PREC_C128) return run_chain<double>(h, adjoint, in, out, nv, st, prof, precision);
+        return run_chain<float>(h, adjoint, in, out, nv, st, prof, precision);
     };
     const bool prof = h->profiling != 0;
     if (!h->use_graphs || st == nullptr) return launch_all(prof);

@@ -122,6 +122,45 @@ struct CoreApplyArgs {
     size_t smem;
 };
 
+// Split-BF16 tensor-core core contraction (tb_core_tc.cu).  A work item is one
+// tile of up to 128 core rows of one pair; its K-chunks of 32 complex columns
+// are stored as consecutive blocks of rows x 256 bytes (hi then lo BF16).
+struct CoreItem {
+    int pair, tile, rows, nkc;
+    int64_t boff;   // byte offset of the item's first block
+};
+
+struct CoreTileArgs {
+    int d, adjoint;
+    int64_t nitems;
+    const CoreItem *items;
+    const int *dims;
+    const int64_t *core_off;
+    const c128 *c128;
+    const c64 *c64;
+    unsigned char *out;
+};
+
+struct CoreTcArgs {
+    int d, adjoint;
+    int64_t nitems;
+    const CoreItem *items;
+    const unsigned char *tiles;
+    const int *dims;
+    const cx<float> *in;
+    cx<float> *out;
+    int in_tsize, out_tsize;
+    int in_R[MAXD], out_R[MAXD];
+    int nv;         // RHS stride of the tiles
+    int v0, nvc;    // RHS chunk [v0, v0 + nvc) handled by this launch, nvc <= 16
+    int *err;
+};
+
+cudaError_t launch_core_tile(const CoreTileArgs &a, cudaStream_t st);
+cudaError_t launch_core_tc(const CoreTcArgs &a, cudaStream_t st);
+int core_tc_rows_per_item();
+int core_tc_cols_per_chunk();
+
 enum class Pass { LeafIn, Split, Gather, LeafOut };
 
 template <class R>

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "tb_common.cuh"
+#include "tb_kernels.cuh"
 
 namespace tb {
 
@@ -77,7 +78,12 @@ struct tb_plan {
     int *core_dims = nullptr;      // P x 2d: target ranks then source ranks (device)
     tb::c128 *core64 = nullptr;
     tb::c64 *core32 = nullptr;
-    tb::c64 *core_bf = nullptr;    // split-BF16 storage (hi, lo) reinterpreted, see tb_core_tc.cu
+    // split-BF16 tiles of the core for the tensor-core contraction: [0] forward
+    // K(t-bar, s-bar), [1] adjoint K(t-bar, s-bar)^H (see tb_core_tc.cu)
+    unsigned char *tc_tiles[2] = {nullptr, nullptr};
+    tb::CoreItem *tc_items[2] = {nullptr, nullptr};
+    int64_t tc_nitems[2] = {0, 0};
+    int64_t tc_bytes[2] = {0, 0};
     int64_t core_entries = 0;
     int64_t core_in_entries = 0;   // sum over pairs of prod_k |s-bar_k| (compact core columns)
     int64_t core_out_entries = 0;  // sum over pairs of prod_k |t-bar_k|

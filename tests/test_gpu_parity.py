@@ -178,6 +178,39 @@ def test_apply_host_matches_device():
     assert np.array_equal(host, dev.astype(np.complex64))
 
 
+# ---------------------------------------------- split-BF16 tensor-core core
+@pytest.mark.parametrize("nv", [16, 5, 20])
+def test_splitbf16_core_matches_c64_and_oracle(nv):
+    # two-term split BF16 with FP32 accumulation keeps ~16 mantissa bits per
+    # product: the apply must agree with the complex64 apply to ~1e-5 and stay
+    # within the workload bound (1e-3 at eps = 1e-4) against the oracle
+    # 4 points per wavelength, as in the n = 256 workload
+    w = W.small("helmholtz3d_n256", 32, nv=nv, L=2, params=(2 * np.pi * 8,))
+    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C64_SPLITBF16))
+    f = W.rhs(w)
+    u32 = run(op, w, f, tb.PREC_C64)
+    ubf = run(op, w, f, tb.PREC_C64_SPLITBF16)
+    assert rel(ubf, u32) < 1e-4
+    ref = oracle.workload_apply(w, f)
+    assert rel(ubf, ref) <= w.bound
+    v32 = run(op, w, f, tb.PREC_C64, adjoint=True)
+    vbf = run(op, w, f, tb.PREC_C64_SPLITBF16, adjoint=True)
+    assert rel(vbf, v32) < 1e-4
+    assert rel(vbf, oracle.workload_apply_adjoint(w, f)) <= w.bound
+
+
+def test_splitbf16_core_multilevel_and_deterministic():
+    w = W.small("helmholtz3d_n256", 64, nv=16, L=4, params=(2 * np.pi * 16,))
+    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C64_SPLITBF16))
+    f = W.rhs(w)
+    rows = W.sample_targets(w, 512)
+    ubf = run(op, w, f, tb.PREC_C64_SPLITBF16)
+    assert rel(ubf, run(op, w, f, tb.PREC_C64)) < 1e-4
+    assert rel(ubf[rows], oracle.workload_apply(w, f, rows)) <= w.bound
+    again = run(op, w, f, tb.PREC_C64_SPLITBF16)
+    assert np.array_equal(ubf, again)
+
+
 # ------------------------------------------------------- benchmark workloads
 def test_config_helmholtz3d_n64_sampled():
     w = W.WORKLOADS["helmholtz3d_n64"]
