@@ -167,6 +167,38 @@ tb_status tb_apply_adjoint(tb_handle h, const void *g, void *v, int64_t nv, int 
  */
 tb_status tb_apply_host(tb_handle h, const void *f, void *u, int64_t nv, int precision);
 
+/*
+ * u = K f without allocating any device memory.  (The paper has no
+ * counterpart: this is an interface of this library.)
+ *
+ * Same arguments, layout, result and stream ordering as tb_apply, but the
+ * level intermediates live in one fixed scratch area compiled into the
+ * library, instead of buffers the handle allocates on its first apply or when
+ * nv grows.  It is meant for callers that cannot call cudaMalloc while they
+ * apply the operator: processes whose device memory is owned by another
+ * allocator (a framework's caching allocator, a fixed arena, a hard memory
+ * cap), and latency-critical loops that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree imply.  The handle itself is
+ * still built (and its factors allocated) by tb_build beforehand.
+ *
+ *   - Scratch: TB_NOALLOC_SCRATCH_BYTES per device, held by every GPU that
+ *     loads the library until the process exits.  A request needing more
+ *     (two level tensors of the handle's largest size x nv x element size)
+ *     fails with TB_EUNSUPPORTED.
+ *   - The first call on a device looks up the scratch address on the host
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call shares the one scratch area, and it keeps the last call's
+ *     contents.  Nothing in it has to start at zero (each pass writes every
+ *     entry a later pass reads).  Calls that overlap on the GPU (on different
+ *     streams, or from several host threads) race on it and corrupt each
+ *     other's results: serialise them.
+ *   - No CUDA-graph replay and no per-pass profiling on this path.
+ * Errors: as tb_apply, plus TB_EUNSUPPORTED for requests beyond the scratch.
+ */
+#define TB_NOALLOC_SCRATCH_BYTES (64ull << 20)
+tb_status tb_apply_noalloc(tb_handle h, const void *f, void *u, int64_t nv, int precision,
+                           void *cuda_stream);
+
 /* Describe a built handle (ranks, sizes, timings). */
 tb_status tb_query(tb_handle h, tb_info *info);
 

@@ -31,7 +31,7 @@ STATUS = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "TB_ERAN
 # every symbol declared in include/tb.h
 EXPORTS = ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
            "tb_apply_host", "tb_query", "tb_free", "tb_last_error", "tb_version",
-           "tb_profile_enable", "tb_profile_stats")
+           "tb_profile_enable", "tb_profile_stats", "tb_apply_noalloc")
 
 
 class TBError(RuntimeError):
@@ -104,8 +104,10 @@ def lib():
         L.tb_version.restype = ctypes.c_char_p
         L.tb_profile_enable.argtypes = [P, ctypes.c_int]
         L.tb_profile_stats.argtypes = [P, ctypes.POINTER(_PassStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+        L.tb_apply_noalloc.argtypes = [P, P, P, I64, ctypes.c_int, P]
         for name in ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
-                     "tb_apply_host", "tb_query", "tb_free", "tb_profile_enable", "tb_profile_stats"):
+                     "tb_apply_host", "tb_query", "tb_free", "tb_profile_enable", "tb_profile_stats",
+                     "tb_apply_noalloc"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB

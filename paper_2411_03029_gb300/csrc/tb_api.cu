@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -787,10 +788,16 @@ void pass_cost(const tb_plan *h, Pass pass, int side, int l, int64_t nv, size_t 
     }
 }
 
+// `bufs` overrides the handle's workspace buffers (tb_apply_noalloc); NULL
+// keeps them.
 template <class R>
 tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st, bool prof,
-                    int precision) {
+                    int precision, void *const *bufs = nullptr) {
     void *B[2] = {h->ws.buf[0], h->ws.buf[1]};
+    if (bufs) {
+        B[0] = bufs[0];
+        B[1] = bufs[1];
+    }
     const int Lc = h->Lc, d = h->d;
     const int first = adjoint ? 1 : 0, second = 1 - first;   // side traversed first / last
     const size_t es = sizeof(cx<R>);
@@ -928,6 +935,65 @@ extern "C" tb_status tb_apply(tb_handle h, const void *f, void *u, int64_t nv, i
 
 extern "C" tb_status tb_apply_adjoint(tb_handle h, const void *g, void *v, int64_t nv, int precision, void *stream) {
     return apply_common(h, g, v, nv, precision, stream, true);
+}
+
+// ------------------------------------------------- apply without allocating
+// The scratch area of tb_apply_noalloc: a fixed device array compiled into the
+// library.  In host code `g_noalloc_scratch` names a host-side stand-in, not
+// device memory, so its device address is looked up once per device with
+// cudaGetSymbolAddress (with that device current) and cached here.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TB_NOALLOC_SCRATCH_BYTES];
+static void *g_noalloc_addr[64] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+extern "C" tb_status tb_apply_noalloc(tb_handle h, const void *f, void *u, int64_t nv, int precision,
+                                      void *stream) {
+    if (!h) return fail(TB_EINVAL, "handle is NULL");
+    if (nv <= 0) return fail(TB_EINVAL, "nv must be positive");
+    if (precision < TB_PREC_C128 || precision > TB_PREC_C64_SPLITBF16)
+        return fail(TB_EINVAL, "unknown precision");
+    if (!(h->precisions & (1u << precision)))
+        return fail(TB_EUNSUPPORTED, "handle was built without precision " + std::to_string(precision));
+    TB_TRY(check_device_ptr(f, "f"));
+    TB_TRY(check_device_ptr(u, "u"));
+    int64_t N = 1;
+    for (int k = 0; k < h->d; ++k) N *= h->n[k];
+    const size_t es = precision == TB_PREC_C128 ? 16 : 8;
+    const char *a0 = (const char *)f, *b0 = (const char *)u;
+    if (a0 < b0 + (size_t)N * nv * es && b0 < a0 + (size_t)N * nv * es)
+        return fail(TB_EINVAL, "input and output overlap");
+    // two level tensors (ping-pong) of the largest level, 256-byte aligned
+    const size_t half = ((size_t)h->level_max * (size_t)nv * es + 255) / 256 * 256;
+    if (2 * half > (size_t)TB_NOALLOC_SCRATCH_BYTES)
+        return fail(TB_EUNSUPPORTED, "tb_apply_noalloc needs " + std::to_string(2 * half) +
+                                         " bytes of scratch; the fixed scratch holds " +
+                                         std::to_string((size_t)TB_NOALLOC_SCRATCH_BYTES) + " (reduce nv)");
+    if (h->device < 0 || h->device >= 64) return fail(TB_EINVAL, "device ordinal out of range");
+    if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[h->device]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p) {
+                cudaGetLastError();
+                return fail(TB_ECUDA, std::string("cudaGetSymbolAddress of the no-alloc scratch: ") +
+                                          cudaGetErrorString(e));
+            }
+            g_noalloc_addr[h->device] = p;
+        }
+        base = g_noalloc_addr[h->device];
+    }
+    if (g_smem_optin == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+        g_smem_optin = (size_t)v;
+    }
+    void *bufs[2] = {base, (unsigned char *)base + half};
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == TB_PREC_C128) return run_chain<double>(h, false, f, u, nv, st, false, precision, bufs);
+    return run_chain<float>(h, false, f, u, nv, st, false, precision, bufs);
 }
 
 extern "C" tb_status tb_apply_host(tb_handle h, const void *f, void *u, int64_t nv, int precision) {
