@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <complex>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -235,7 +236,8 @@ static tb_status build_cores(tb_plan *h) {
         const int nb = 1 << Lc;
         for (int k = 0; k < d; ++k) {
             const int64_t cnt = (int64_t)nb * nb * T.R[k] * S.R[k];
-            if (want64) TB_TRY(dalloc(h, &h->kron64[k], cnt));
+            (void)want64;   // FP64 per-mode cores are always kept: they feed the separable chains
+            TB_TRY(dalloc(h, &h->kron64[k], cnt));
             if (want32) TB_TRY(dalloc(h, &h->kron32[k], cnt));
             KronArgs a;
             a.Lc = Lc;
@@ -360,6 +362,233 @@ extern "C" tb_status tb_build(const tb_kernel *kernel, int d, const int64_t *n, 
     return tb_build_ex(kernel, d, n, grids, tol, nullptr, out);
 }
 
+// --------------------------------------------------- separable (per-mode) chains
+namespace {
+
+struct HostStep {
+    int n_out = 0, n_in = 0;
+    std::vector<int> rowptr, col;
+    std::vector<std::complex<double>> val;
+};
+
+// Sparse step built row by row: rows are appended in order, explicit zeros dropped.
+struct StepBuilder {
+    HostStep s;
+    StepBuilder(int n_out, int n_in) {
+        s.n_out = n_out;
+        s.n_in = n_in;
+        s.rowptr.push_back(0);
+    }
+    void add(int c, std::complex<double> v) {
+        if (v != std::complex<double>(0.0, 0.0)) {
+            s.col.push_back(c);
+            s.val.push_back(v);
+        }
+    }
+    void end_row() { s.rowptr.push_back((int)s.col.size()); }
+};
+
+HostStep conj_transpose(const HostStep &a) {
+    HostStep t;
+    t.n_out = a.n_in;
+    t.n_in = a.n_out;
+    std::vector<std::vector<std::pair<int, std::complex<double>>>> rows((size_t)a.n_in);
+    for (int r = 0; r < a.n_out; ++r)
+        for (int j = a.rowptr[(size_t)r]; j < a.rowptr[(size_t)r + 1]; ++j)
+            rows[(size_t)a.col[(size_t)j]].push_back({r, std::conj(a.val[(size_t)j])});
+    t.rowptr.push_back(0);
+    for (auto &row : rows) {
+        for (auto &e : row) {
+            t.col.push_back(e.first);
+            t.val.push_back(e.second);
+        }
+        t.rowptr.push_back((int)t.col.size());
+    }
+    return t;
+}
+
+}  // namespace
+
+// The per-mode chains of a separable handle: step matrices on the 1-D index
+// of mode k, assembled from the factor blocks (which depend on the mode-k
+// nodes only).  Source level l index: ((s 2^l + tau) 2^(Lc-l) + nu) R_l + a;
+// target level l index: ((t 2^l + nu) 2^(Lc-l) + tau) R_l + a.
+static tb_status build_sep_steps(tb_plan *h) {
+    const int d = h->d, Lc = h->Lc, L = h->L;
+    using C = std::complex<double>;
+    auto fetch = [&](const c128 *p, int64_t n, std::vector<C> &out) -> tb_status {
+        std::vector<c128> tmp((size_t)n);
+        TB_CK(cudaMemcpy(tmp.data(), p, (size_t)n * sizeof(c128), cudaMemcpyDeviceToHost));
+        out.resize((size_t)n);
+        for (int64_t i = 0; i < n; ++i) out[(size_t)i] = C(tmp[(size_t)i].x, tmp[(size_t)i].y);
+        return TB_OK;
+    };
+    std::vector<HostStep> all[2];
+    for (int k = 0; k < d; ++k) {
+        const int nk = (int)h->n[k], cb = (int)h->cb[k], nmid = nk >> Lc, nb = 1 << Lc;
+        std::vector<int> perm((size_t)nk);
+        const int bits = ilog2(nk);
+        for (int p = 0; p < nk; ++p) {
+            int q = p;
+            if (h->order == TB_ORDER_BITREV) {
+                q = 0;
+                for (int b = 0; b < bits; ++b) q |= ((p >> b) & 1) << (bits - 1 - b);
+            }
+            perm[(size_t)p] = q;
+        }
+        std::vector<std::vector<C>> fs(Lc + 1), ft(Lc + 1);
+        for (int l = 0; l <= Lc; ++l) {
+            TB_TRY(fetch(h->src[l].fac64[k], h->src[l].count[k] * h->src[l].R[k] * h->src[l].cin[k], fs[l]));
+            TB_TRY(fetch(h->tgt[l].fac64[k], h->tgt[l].count[k] * h->tgt[l].R[k] * h->tgt[l].cin[k], ft[l]));
+        }
+        std::vector<C> kr;
+        const int Rt = h->tgt[Lc].R[k], Rs = h->src[Lc].R[k];
+        TB_TRY(fetch(h->kron64[k], (int64_t)nb * nb * Rt * Rs, kr));
+        auto Rsrc = [&](int l) { return h->src[l].R[k]; };
+        auto Rtgt = [&](int l) { return h->tgt[l].R[k]; };
+        auto esrc = [&](int l, int s, int tau, int nu, int a) {
+            return ((((s << l) + tau) << (Lc - l)) + nu) * Rsrc(l) + a;
+        };
+        auto etgt = [&](int l, int t, int nu, int tau, int a) {
+            return ((((t << l) + nu) << (Lc - l)) + tau) * Rtgt(l) + a;
+        };
+        // factor block (F, M, sig) of side-level data, R x cin, row-major
+        auto blk = [&](const std::vector<C> &f, const SideLevel &S, int l, int F, int M, int sig, int a, int c) {
+            const int64_t j = ((((int64_t)F << l) + M) << (Lc - l)) + sig;
+            return f[(size_t)((j * S.R[k] + a) * S.cin[k] + c)];
+        };
+        std::vector<HostStep> st;
+        // source leaves: V
+        {
+            StepBuilder b(esrc(0, nb - 1, 0, nb - 1, Rsrc(0) - 1) + 1, nk);
+            for (int s = 0; s < nb; ++s)
+                for (int nu = 0; nu < nb; ++nu)
+                    for (int a = 0; a < Rsrc(0); ++a) {
+                        for (int c = 0; c < cb; ++c)
+                            b.add(perm[(size_t)(s * nmid + nu * cb + c)], blk(fs[0], h->src[0], 0, s, 0, nu, a, c));
+                        b.end_row();
+                    }
+            st.push_back(b.s);
+        }
+        // source transfers: W
+        for (int l = 1; l <= Lc; ++l) {
+            const int ns = 1 << (Lc - l);
+            StepBuilder b(nb * (1 << l) * ns * Rsrc(l), nb * (1 << (l - 1)) * 2 * ns * Rsrc(l - 1));
+            for (int s = 0; s < nb; ++s)
+                for (int tau = 0; tau < (1 << l); ++tau)
+                    for (int nu = 0; nu < ns; ++nu)
+                        for (int a = 0; a < Rsrc(l); ++a) {
+                            for (int c = 0; c < 2; ++c)
+                                for (int q = 0; q < Rsrc(l - 1); ++q)
+                                    b.add(esrc(l - 1, s, tau >> 1, 2 * nu + c, q),
+                                          blk(fs[l], h->src[l], l, s, tau, nu, a, c * Rsrc(l - 1) + q));
+                            b.end_row();
+                        }
+            st.push_back(b.s);
+        }
+        // core: K_k(t-bar_k, s-bar_k)
+        {
+            StepBuilder b(nb * nb * Rt, nb * nb * Rs);
+            for (int t = 0; t < nb; ++t)
+                for (int s = 0; s < nb; ++s)
+                    for (int a = 0; a < Rt; ++a) {
+                        for (int q = 0; q < Rs; ++q)
+                            b.add(esrc(Lc, s, t, 0, q), kr[(size_t)(((int64_t)t * nb + s) * Rt * Rs + a * Rs + q)]);
+                        b.end_row();
+                    }
+            st.push_back(b.s);
+        }
+        // target transfers: P (gather over the two children of each source node)
+        for (int l = Lc; l >= 1; --l) {
+            const int ns = 1 << (Lc - l);
+            StepBuilder b(nb * (1 << (l - 1)) * 2 * ns * Rtgt(l - 1), nb * (1 << l) * ns * Rtgt(l));
+            for (int t = 0; t < nb; ++t)
+                for (int pn = 0; pn < (1 << (l - 1)); ++pn)
+                    for (int tp = 0; tp < 2 * ns; ++tp)
+                        for (int a = 0; a < Rtgt(l - 1); ++a) {
+                            for (int c = 0; c < 2; ++c)
+                                for (int q = 0; q < Rtgt(l); ++q)
+                                    b.add(etgt(l, t, 2 * pn + c, tp >> 1, q),
+                                          blk(ft[l], h->tgt[l], l, t, 2 * pn + c, tp >> 1, q,
+                                              (tp & 1) * Rtgt(l - 1) + a));
+                            b.end_row();
+                        }
+            st.push_back(b.s);
+        }
+        // target leaves: U^T, rows in grid order
+        {
+            StepBuilder b(nk, nb * nb * Rtgt(0));
+            std::vector<int> owner((size_t)nk);
+            for (int p = 0; p < nk; ++p) owner[(size_t)perm[(size_t)p]] = p;
+            for (int g = 0; g < nk; ++g) {
+                const int p = owner[(size_t)g];
+                const int t = p / nmid, tau = (p % nmid) / cb, a = p % cb;
+                for (int q = 0; q < Rtgt(0); ++q) b.add(etgt(0, t, 0, tau, q), blk(ft[0], h->tgt[0], 0, t, 0, tau, q, a));
+                b.end_row();
+            }
+            st.push_back(b.s);
+        }
+        int mx = nk;
+        for (auto &s : st) mx = std::max({mx, s.n_out, s.n_in});
+        h->sep_maxext[k] = mx;
+        h->sep_step0[0][k] = (int)all[0].size();
+        h->sep_nsteps[0][k] = (int)st.size();
+        h->sep_step0[1][k] = (int)all[1].size();
+        h->sep_nsteps[1][k] = (int)st.size();
+        for (auto &s : st) {
+            h->sep_nnz[0][k] += (int64_t)s.col.size();
+            all[0].push_back(s);
+        }
+        for (auto it = st.rbegin(); it != st.rend(); ++it) {   // adjoint: reversed, conjugate transposed
+            all[1].push_back(conj_transpose(*it));
+            h->sep_nnz[1][k] += (int64_t)it->col.size();
+        }
+    }
+    // upload: shared index arrays, FP64 and FP32 values, step descriptors
+    for (int dir = 0; dir < 2; ++dir) {
+        std::vector<int> idx;
+        std::vector<c128> v64;
+        std::vector<c64> v32;
+        std::vector<std::pair<int64_t, int64_t>> off;   // (rowptr offset, col/val offset)
+        for (auto &s : all[dir]) {
+            off.push_back({(int64_t)idx.size(), (int64_t)v64.size()});
+            idx.insert(idx.end(), s.rowptr.begin(), s.rowptr.end());
+            for (size_t j = 0; j < s.col.size(); ++j) {
+                v64.push_back(c128{s.val[j].real(), s.val[j].imag()});
+                v32.push_back(c64{(float)s.val[j].real(), (float)s.val[j].imag()});
+            }
+        }
+        std::vector<int> cols;
+        for (auto &s : all[dir]) cols.insert(cols.end(), s.col.begin(), s.col.end());
+        int *d_idx = nullptr, *d_col = nullptr;
+        c128 *d_v64 = nullptr;
+        c64 *d_v32 = nullptr;
+        TB_TRY(dalloc(h, &d_idx, (int64_t)std::max<size_t>(idx.size(), 1)));
+        TB_TRY(dalloc(h, &d_col, (int64_t)std::max<size_t>(cols.size(), 1)));
+        TB_TRY(dalloc(h, &d_v64, (int64_t)std::max<size_t>(v64.size(), 1)));
+        TB_TRY(dalloc(h, &d_v32, (int64_t)std::max<size_t>(v32.size(), 1)));
+        TB_CK(cudaMemcpy(d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+        TB_CK(cudaMemcpy(d_col, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice));
+        TB_CK(cudaMemcpy(d_v64, v64.data(), v64.size() * sizeof(c128), cudaMemcpyHostToDevice));
+        TB_CK(cudaMemcpy(d_v32, v32.data(), v32.size() * sizeof(c64), cudaMemcpyHostToDevice));
+        std::vector<SepStep<double>> s64;
+        std::vector<SepStep<float>> s32;
+        for (size_t i = 0; i < all[dir].size(); ++i) {
+            const HostStep &s = all[dir][i];
+            s64.push_back(SepStep<double>{s.n_out, s.n_in, d_idx + off[i].first, d_col + off[i].second,
+                                          d_v64 + off[i].second});
+            s32.push_back(SepStep<float>{s.n_out, s.n_in, d_idx + off[i].first, d_col + off[i].second,
+                                         d_v32 + off[i].second});
+        }
+        TB_TRY(dalloc(h, &h->sep64[dir], (int64_t)s64.size()));
+        TB_TRY(dalloc(h, &h->sep32[dir], (int64_t)s32.size()));
+        TB_CK(cudaMemcpy(h->sep64[dir], s64.data(), s64.size() * sizeof(s64[0]), cudaMemcpyHostToDevice));
+        TB_CK(cudaMemcpy(h->sep32[dir], s32.data(), s32.size() * sizeof(s32[0]), cudaMemcpyHostToDevice));
+    }
+    (void)L;
+    return TB_OK;
+}
+
 static tb_status build_impl(tb_plan *h, const tb_grids *grids) {
     const int d = h->d;
     TB_TRY(dalloc(h, &h->d_err, 1));
@@ -405,6 +634,12 @@ static tb_status build_impl(tb_plan *h, const tb_grids *grids) {
         lm = std::max(lm, h->P * prod_tile(h->tgt[l], d));
     }
     h->level_max = lm;
+    if (h->separable) {
+        TB_TRY(build_sep_steps(h));
+        int64_t N = 1;
+        for (int k = 0; k < d; ++k) N *= h->n[k];
+        h->level_max = std::max(h->level_max, N);   // the per-mode passes ping-pong full tensors
+    }
     TB_CK(cudaDeviceSynchronize());
     return TB_OK;
 }
@@ -788,6 +1023,96 @@ void pass_cost(const tb_plan *h, Pass pass, int side, int l, int64_t nv, size_t 
     }
 }
 
+template <class R>
+const SepStep<R> *sepptr(const tb_plan *h, int dir);
+template <>
+const SepStep<double> *sepptr<double>(const tb_plan *h, int dir) { return h->sep64[dir]; }
+template <>
+const SepStep<float> *sepptr<float>(const tb_plan *h, int dir) { return h->sep32[dir]; }
+
+// Separable handle: per-mode chains applied in passes over up to three
+// consecutive modes (from the last mode down), ping-ponging full tensors.
+template <class R>
+tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st, bool prof,
+                  void *const *B) {
+    const int d = h->d, dir = adjoint ? 1 : 0;
+    const int64_t es = sizeof(cx<R>);
+    const int64_t limit = 96 * 1024;
+    int64_t N = 1;
+    for (int k = 0; k < d; ++k) N *= h->n[k];
+    struct Plan {
+        int k0, k1;
+        int64_t ic, buf;
+    };
+    std::vector<Plan> plan;
+    auto bufsz = [&](int k0, int k1) {
+        int64_t b = 0;
+        for (int k = k0; k <= k1; ++k) {
+            int64_t t = h->sep_maxext[k];
+            for (int j = k0; j <= k1; ++j)
+                if (j != k) t *= h->n[j];
+            b = std::max(b, t);
+        }
+        return b;
+    };
+    for (int k1 = d - 1; k1 >= 0;) {
+        int64_t inner = nv;
+        for (int k = k1 + 1; k < d; ++k) inner *= h->n[k];
+        const int64_t icmin = std::min<int64_t>(inner, 8);   // keep >= 64 contiguous bytes per fiber
+        int k0 = k1;
+        while (k0 > 0 && k1 - k0 < 2 && 2 * bufsz(k0 - 1, k1) * icmin * es <= limit) --k0;
+        const int64_t b = bufsz(k0, k1);
+        const int64_t ic = std::max<int64_t>(1, std::min<int64_t>(inner, limit / (2 * b * es)));
+        if ((size_t)(2 * b * ic * es) > g_smem_optin)
+            return fail(TB_EUNSUPPORTED, "per-mode pass needs more shared memory than the device has");
+        plan.push_back(Plan{k0, k1, ic, b * ic});
+        k1 = k0 - 1;
+    }
+    for (size_t i = 0; i < plan.size(); ++i) {
+        const Plan &pl = plan[i];
+        SepPassArgs<R> a;
+        std::memset(&a, 0, sizeof(a));
+        a.d = d;
+        a.k0 = pl.k0;
+        a.k1 = pl.k1;
+        for (int k = 0; k < d; ++k) a.n[k] = (int)h->n[k];
+        a.outer = 1;
+        for (int k = 0; k < pl.k0; ++k) a.outer *= h->n[k];
+        a.inner = nv;
+        for (int k = pl.k1 + 1; k < d; ++k) a.inner *= h->n[k];
+        a.ic = (int)pl.ic;
+        a.nchunks = (a.inner + a.ic - 1) / a.ic;
+        // pass i reads the user input (i = 0) or buffer (i-1) % 2 and writes
+        // buffer i % 2, the last pass writes the user output
+        a.in = (const cx<R> *)(i == 0 ? in : B[(i - 1) & 1]);
+        a.out = (cx<R> *)(i + 1 == plan.size() ? out : B[i & 1]);
+        a.steps = sepptr<R>(h, dir);
+        for (int k = 0; k < d; ++k) {
+            a.step0[k] = h->sep_step0[dir][k];
+            a.nsteps[k] = h->sep_nsteps[dir][k];
+        }
+        a.buf = (int)pl.buf;
+        a.smem = (size_t)(2 * pl.buf * es);
+        ProfRec r{"sep_pass", (int)i, (int)adjoint, nullptr, nullptr, 0, 0.0};
+        if (prof) {
+            r.bytes = 2 * N * nv * es;
+            for (int k = pl.k0; k <= pl.k1; ++k) {
+                r.bytes += h->sep_nnz[dir][k] * (es + 4);
+                r.flops += 8.0 * (double)h->sep_nnz[dir][k] * (double)(N / h->n[k]) * (double)nv;
+            }
+            TB_CK(cudaEventCreate(&r.e0));
+            TB_CK(cudaEventCreate(&r.e1));
+            TB_CK(cudaEventRecord(r.e0, st));
+        }
+        TB_CK(launch_sep_pass<R>(a, st));
+        if (prof) {
+            TB_CK(cudaEventRecord(r.e1, st));
+            h->prof.push_back(r);
+        }
+    }
+    return TB_OK;
+}
+
 // `bufs` overrides the handle's workspace buffers (tb_apply_noalloc); NULL
 // keeps them.
 template <class R>
@@ -798,6 +1123,7 @@ tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t
         B[0] = bufs[0];
         B[1] = bufs[1];
     }
+    if (h->separable) return run_sep<R>(h, adjoint, in, out, nv, st, prof, B);
     const int Lc = h->Lc, d = h->d;
     const int first = adjoint ? 1 : 0, second = 1 - first;   // side traversed first / last
     const size_t es = sizeof(cx<R>);

@@ -161,6 +161,38 @@ cudaError_t launch_core_tc(const CoreTcArgs &a, cudaStream_t st);
 int core_tc_rows_per_item();
 int core_tc_cols_per_chunk();
 
+// Separable kernels (a product over modes): every factor depends on one mode,
+// so the butterfly is a tensor product of per-mode 1-D butterflies.  Each
+// mode's chain (leaf V, transfers W, core K_k, transfers P, leaf U) is stored
+// as a list of sparse step matrices (CSR, explicit zeros dropped) acting on
+// the 1-D index of that mode.
+template <class R>
+struct SepStep {
+    int n_out, n_in;
+    const int *rowptr;   // n_out + 1
+    const int *col;
+    const cx<R> *val;
+};
+
+template <class R>
+struct SepPassArgs {
+    int d, k0, k1;            // modes k0..k1 (contiguous) are transformed by this pass
+    int n[MAXD];
+    int64_t outer;            // prod_{k < k0} n_k
+    int64_t inner;            // nv * prod_{k > k1} n_k (contiguous in memory)
+    int ic;                   // inner elements per block
+    int64_t nchunks;          // ceil(inner / ic)
+    const cx<R> *in;
+    cx<R> *out;
+    const SepStep<R> *steps;  // device array
+    int step0[MAXD], nsteps[MAXD];
+    int buf;                  // elements of each of the two shared buffers
+    size_t smem;
+};
+
+template <class R>
+cudaError_t launch_sep_pass(const SepPassArgs<R> &a, cudaStream_t st);
+
 enum class Pass { LeafIn, Split, Gather, LeafOut };
 
 template <class R>

@@ -93,6 +93,14 @@ struct tb_plan {
     tb::c128 *kron64[TB_MAX_D] = {nullptr};
     tb::c64 *kron32[TB_MAX_D] = {nullptr};
 
+    // separable chains: per direction (0 forward, 1 adjoint) the step
+    // descriptors of every mode, FP64 and FP32 values
+    tb::SepStep<double> *sep64[2] = {nullptr, nullptr};
+    tb::SepStep<float> *sep32[2] = {nullptr, nullptr};
+    int sep_step0[2][TB_MAX_D] = {{0}}, sep_nsteps[2][TB_MAX_D] = {{0}};
+    int sep_maxext[TB_MAX_D] = {0};   // largest 1-D index along a mode's chain
+    int64_t sep_nnz[2][TB_MAX_D] = {{0}};
+
     int64_t level_max = 0;         // largest level tensor, entries per RHS
     tb::Workspace ws;
     std::vector<tb::GraphEntry> graphs;

@@ -61,6 +61,32 @@ def test_fourier_bitrev_is_exact(d, n, L, separable):
     assert rel(u32, ref) < 2e-6
 
 
+@pytest.mark.parametrize("d,n,L,nv", [(4, 8, 2, 3), (6, 4, 2, 2)])
+def test_separable_high_dimension_full_output(d, n, L, nv):
+    w = W.Workload(name="f", kind=W.FOURIER, d=d, n=n, tol=1e-8, nv=nv, precision=W.C128, bound=1e-12,
+                   rhs_seeds=tuple(range(nv)), samples=0, order=W.ORDER_BITREV, L=L)
+    op = tb.from_workload(w)
+    assert op.info()["separable"] == 1
+    f = W.rhs(w)
+    ref = oracle.fourier_fft(f.numpy(), d).reshape(-1, nv)
+    assert rel(run(op, w, f, tb.PREC_C128), ref) < 1e-12
+    assert rel(run(op, w, f, tb.PREC_C64), ref) < 1e-5
+    assert rel(run(op, w, f, tb.PREC_C128, adjoint=True), oracle.workload_apply_adjoint(w, f)) < 1e-12
+
+
+def test_config_fourier6d_n16_sampled():
+    w = W.WORKLOADS["fourier6d_n16"]
+    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C128))
+    f = W.rhs(w)
+    rows = W.sample_targets(w, 128)
+    ref = oracle.workload_apply(w, f, rows)
+    u = run(op, w, f, tb.PREC_C64, rows)
+    assert rel(u, ref) <= w.bound
+    assert rel(run(op, w, f, tb.PREC_C128, rows), ref) < 1e-12
+    cols = W.sample_targets(w, 64, seed=77)
+    assert rel(run(op, w, f, tb.PREC_C64, cols, adjoint=True), oracle.workload_apply_adjoint(w, f, cols)) <= w.bound
+
+
 def test_config_fourier2d_n64_full_output():
     w = W.WORKLOADS["fourier2d_n64"]
     op = tb.from_workload(w)
