@@ -272,7 +272,8 @@ def main():
     stats = op.profile_stats()
     ms = max_over_ranks(ws, ms)
     value = ws * N * nv / (ms * 1e-3) / 1e9
-    launches_per_step = 2 * info["Lc"] + 3
+    # kernel launches of one apply, counted from the per-pass event records
+    launches_per_step = int(round(sum(s["launches"] for s in stats) / max(args.steps, 1))) if stats else 0
 
     pk = peaks()
     dom = max(stats, key=lambda s: s["ms_total"]) if stats else None

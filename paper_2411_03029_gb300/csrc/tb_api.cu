@@ -537,11 +537,13 @@ static tb_status build_sep_steps(tb_plan *h) {
         h->sep_nsteps[1][k] = (int)st.size();
         for (auto &s : st) {
             h->sep_nnz[0][k] += (int64_t)s.col.size();
+            h->sep_nidx[0][k] += s.n_out + 1;
             all[0].push_back(s);
         }
         for (auto it = st.rbegin(); it != st.rend(); ++it) {   // adjoint: reversed, conjugate transposed
             all[1].push_back(conj_transpose(*it));
             h->sep_nnz[1][k] += (int64_t)it->col.size();
+            h->sep_nidx[1][k] += it->n_in + 1;
         }
     }
     // upload: shared index arrays, FP64 and FP32 values, step descriptors
@@ -1040,6 +1042,57 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
     const int64_t limit = 96 * 1024;
     int64_t N = 1;
     for (int k = 0; k < d; ++k) N *= h->n[k];
+    // thread-per-fiber passes, one per mode, when every mode's chain fits a
+    // shared-memory column of at least 32 threads per block
+    {
+        int threads[TB_MAX_D];
+        size_t smem[TB_MAX_D];
+        bool fits = true;
+        for (int k = 0; k < d && fits; ++k) {
+            const int64_t fixed = h->sep_nnz[dir][k] * (es + 4) + h->sep_nidx[dir][k] * 4;
+            int T = 256;
+            while (T >= 32 && 2 * h->sep_maxext[k] * T * es + fixed > limit) T /= 2;
+            threads[k] = T;
+            smem[k] = (size_t)(2 * h->sep_maxext[k] * T * es + fixed + 16);
+            fits = T >= 32;
+        }
+        if (fits) {
+            int i = 0;
+            for (int k = d - 1; k >= 0; --k, ++i) {
+                SepFiberArgs<R> a;
+                std::memset(&a, 0, sizeof(a));
+                a.k = k;
+                a.nk = (int)h->n[k];
+                a.outer = 1;
+                for (int j = 0; j < k; ++j) a.outer *= h->n[j];
+                a.inner = nv;
+                for (int j = k + 1; j < d; ++j) a.inner *= h->n[j];
+                a.in = (const cx<R> *)(i == 0 ? in : B[(i - 1) & 1]);
+                a.out = (cx<R> *)(k == 0 ? out : B[i & 1]);
+                a.steps = sepptr<R>(h, dir) + h->sep_step0[dir][k];
+                a.nsteps = h->sep_nsteps[dir][k];
+                a.maxext = h->sep_maxext[k];
+                a.nnz = (int)h->sep_nnz[dir][k];
+                a.nidx = (int)h->sep_nidx[dir][k];
+                a.threads = threads[k];
+                a.smem = smem[k];
+                ProfRec r{"sep_mode", k, (int)adjoint, nullptr, nullptr, 0, 0.0};
+                if (prof) {
+                    r.bytes = 2 * N * nv * es + h->sep_nnz[dir][k] * (es + 4);
+                    r.flops = 8.0 * (double)h->sep_nnz[dir][k] * (double)(N / h->n[k]) * (double)nv;
+                    TB_CK(cudaEventCreate(&r.e0));
+                    TB_CK(cudaEventCreate(&r.e1));
+                    TB_CK(cudaEventRecord(r.e0, st));
+                }
+                TB_CK(launch_sep_fiber<R>(a, st));
+                if (prof) {
+                    TB_CK(cudaEventRecord(r.e1, st));
+                    h->prof.push_back(r);
+                }
+            }
+            return TB_OK;
+        }
+    }
     struct Plan {
         int k0, k1;
         int64_t ic, buf;

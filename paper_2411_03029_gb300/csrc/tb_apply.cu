@@ -227,8 +227,11 @@ __global__ void __launch_bounds__(AP_THREADS) k_level(const LevelArgs<R> a) {
     cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
     cx<R> *X = sm + a.offX, *B0 = sm + a.offB0, *B1 = sm + a.offB1, *Y = sm + a.offY, *Asm = sm + a.offA;
     const int d = a.d, Lc = a.Lc;
-    const int64_t g = blockIdx.x;
-    const int64_t v0 = (int64_t)blockIdx.y * a.nvc;
+    // RHS chunks of one group are consecutive blocks, so the group's tiles are
+    // re-read from L2 rather than DRAM when nv is split into several chunks
+    const int64_t nch = (a.nv + a.nvc - 1) / a.nvc;
+    const int64_t g = blockIdx.x / nch;
+    const int64_t v0 = (int64_t)(blockIdx.x - g * nch) * a.nvc;
     const int nvc = (int)((a.nv - v0) < a.nvc ? (a.nv - v0) : a.nvc);
     const int tid = threadIdx.x;
 
@@ -385,7 +388,7 @@ __global__ void __launch_bounds__(AP_THREADS) k_level(const LevelArgs<R> a) {
 template <class R>
 cudaError_t launch_level(Pass pass, bool conj, const LevelArgs<R> &a, cudaStream_t st) {
     const int64_t nchunks = (a.nv + a.nvc - 1) / a.nvc;
-    dim3 grid((unsigned)a.nblocks, (unsigned)nchunks);
+    dim3 grid((unsigned)(a.nblocks * nchunks));
     void (*fn)(const LevelArgs<R>) = nullptr;
 #define TB_PICK(P)                                                  \
     fn = conj ? k_level<R, P, true> : k_level<R, P, false>;
@@ -410,8 +413,9 @@ __global__ void __launch_bounds__(AP_THREADS) k_core_dense(const CoreApplyArgs<R
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<R> *Xc = reinterpret_cast<cx<R> *>(smraw);
     const int d = a.d;
-    const int64_t p = blockIdx.x;
-    const int64_t v0 = (int64_t)blockIdx.y * a.nvc;
+    const int64_t nch = (a.nv + a.nvc - 1) / a.nvc;
+    const int64_t p = blockIdx.x / nch;
+    const int64_t v0 = (int64_t)(blockIdx.x - p * nch) * a.nvc;
     const int nvc = (int)((a.nv - v0) < a.nvc ? (a.nv - v0) : a.nvc);
     int rt[MAXD], rs[MAXD];
     int Mt = 1, Ms = 1;
@@ -501,7 +505,7 @@ __global__ void __launch_bounds__(AP_THREADS) k_core_dense(const CoreApplyArgs<R
 template <class R>
 cudaError_t launch_core_dense(bool adjoint, const CoreApplyArgs<R> &a, cudaStream_t st) {
     const int64_t nchunks = (a.nv + a.nvc - 1) / a.nvc;
-    dim3 grid((unsigned)a.P, (unsigned)nchunks);
+    dim3 grid((unsigned)(a.P * nchunks));
     void (*fn)(const CoreApplyArgs<R>, int);
     if (a.nvc <= 1) fn = k_core_dense<R, 1>;
     else if (a.nvc <= 4) fn = k_core_dense<R, 4>;
@@ -522,8 +526,9 @@ __global__ void __launch_bounds__(AP_THREADS) k_core_kron(const CoreApplyArgs<R>
     cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
     cx<R> *X = sm + a.offX, *B0 = sm + a.offB0, *B1 = sm + a.offB1, *Y = sm + a.offY, *Asm = sm + a.offA;
     const int d = a.d;
-    const int64_t p = blockIdx.x;
-    const int64_t v0 = (int64_t)blockIdx.y * a.nvc;
+    const int64_t nch = (a.nv + a.nvc - 1) / a.nvc;
+    const int64_t p = blockIdx.x / nch;
+    const int64_t v0 = (int64_t)(blockIdx.x - p * nch) * a.nvc;
     const int nvc = (int)((a.nv - v0) < a.nvc ? (a.nv - v0) : a.nvc);
     const int64_t nb = (int64_t)1 << a.Lc;
     const int64_t nF = (int64_t)1 << (a.Lc * d);
@@ -556,7 +561,7 @@ __global__ void __launch_bounds__(AP_THREADS) k_core_kron(const CoreApplyArgs<R>
 template <class R>
 cudaError_t launch_core_kron(bool adjoint, const CoreApplyArgs<R> &a, cudaStream_t st) {
     const int64_t nchunks = (a.nv + a.nvc - 1) / a.nvc;
-    dim3 grid((unsigned)a.P, (unsigned)nchunks);
+    dim3 grid((unsigned)(a.P * nchunks));
     void (*fn)(const CoreApplyArgs<R>) = adjoint ? k_core_kron<R, true> : k_core_kron<R, false>;
     cudaError_t e = set_smem_once((const void *)fn, a.smem);
     if (e != cudaSuccess) return e;

@@ -193,6 +193,25 @@ struct SepPassArgs {
 template <class R>
 cudaError_t launch_sep_pass(const SepPassArgs<R> &a, cudaStream_t st);
 
+// One mode's chain applied fiber by fiber: thread = (fiber, RHS), the fiber
+// held in a shared-memory column of that thread.
+template <class R>
+struct SepFiberArgs {
+    int k, nk;
+    int64_t outer;            // prod_{j < k} n_j
+    int64_t inner;            // nv * prod_{j > k} n_j
+    const cx<R> *in;
+    cx<R> *out;
+    const SepStep<R> *steps;  // this mode's steps, in order
+    int nsteps, maxext;
+    int nnz, nidx;            // total nonzeros / row-pointer entries of the steps
+    int threads;
+    size_t smem;
+};
+
+template <class R>
+cudaError_t launch_sep_fiber(const SepFiberArgs<R> &a, cudaStream_t st);
+
 enum class Pass { LeafIn, Split, Gather, LeafOut };
 
 template <class R>

@@ -100,6 +100,7 @@ struct tb_plan {
     int sep_step0[2][TB_MAX_D] = {{0}}, sep_nsteps[2][TB_MAX_D] = {{0}};
     int sep_maxext[TB_MAX_D] = {0};   // largest 1-D index along a mode's chain
     int64_t sep_nnz[2][TB_MAX_D] = {{0}};
+    int64_t sep_nidx[2][TB_MAX_D] = {{0}};   // row-pointer entries of a mode's steps
 
     int64_t level_max = 0;         // largest level tensor, entries per RHS
     tb::Workspace ws;

@@ -81,4 +81,76 @@ cudaError_t launch_sep_pass(const SepPassArgs<R> &a, cudaStream_t st) {
 template cudaError_t launch_sep_pass<float>(const SepPassArgs<float> &, cudaStream_t);
 template cudaError_t launch_sep_pass<double>(const SepPassArgs<double> &, cudaStream_t);
 
+// Thread-per-fiber form: each thread owns one (fiber along mode k, RHS) pair
+// and keeps the fiber in its own column of two shared buffers (column-major
+// per thread: entry e of thread t at e * T + t, conflict-free), so the steps
+// of the chain need no block-wide synchronisation.  The steps' nonzeros sit in
+// shared memory and are read as broadcasts.
+template <class R>
+__global__ void k_sep_fiber(const SepFiberArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int T = blockDim.x, t = threadIdx.x;
+    cx<R> *b0 = reinterpret_cast<cx<R> *>(smraw);
+    cx<R> *b1 = b0 + (size_t)a.maxext * T;
+    cx<R> *sval = b1 + (size_t)a.maxext * T;
+    int *sidx = reinterpret_cast<int *>(sval + a.nnz);   // row pointers, then columns
+    __shared__ int s_rp[40], s_cv[40];                    // per-step offsets
+    if (t == 0) {
+        int rp = 0, cv = 0;
+        for (int s = 0; s < a.nsteps; ++s) {
+            s_rp[s] = rp;
+            s_cv[s] = cv;
+            rp += a.steps[s].n_out + 1;
+            cv += a.steps[s].rowptr[a.steps[s].n_out];
+        }
+    }
+    __syncthreads();
+    for (int s = 0; s < a.nsteps; ++s) {
+        const SepStep<R> S = a.steps[s];
+        const int nz = S.rowptr[S.n_out];
+        for (int i = t; i <= S.n_out; i += T) sidx[s_rp[s] + i] = S.rowptr[i];
+        for (int i = t; i < nz; i += T) {
+            sidx[a.nidx + s_cv[s] + i] = S.col[i];
+            sval[s_cv[s] + i] = S.val[i];
+        }
+    }
+    __syncthreads();
+    const int64_t gid = (int64_t)blockIdx.x * T + t;
+    const bool live = gid < a.outer * a.inner;
+    const int64_t o = live ? gid / a.inner : 0, q = live ? gid - o * a.inner : 0;
+    const int64_t base = o * a.nk * a.inner + q;
+    if (live)
+        for (int i = 0; i < a.nk; ++i) b0[i * T + t] = a.in[base + (int64_t)i * a.inner];
+    cx<R> *src = b0, *dst = b1;
+    for (int s = 0; s < a.nsteps; ++s) {
+        const int nout = a.steps[s].n_out;
+        const int *rp = sidx + s_rp[s];
+        const int *cl = sidx + a.nidx + s_cv[s];
+        const cx<R> *vl = sval + s_cv[s];
+        for (int r = 0; r < nout; ++r) {
+            cx<R> acc = {R(0), R(0)};
+            for (int j = rp[r]; j < rp[r + 1]; ++j) cmac(acc, vl[j], src[cl[j] * T + t]);
+            dst[r * T + t] = acc;
+        }
+        cx<R> *tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    if (live)
+        for (int i = 0; i < a.nk; ++i) a.out[base + (int64_t)i * a.inner] = src[i * T + t];
+}
+
+template <class R>
+cudaError_t launch_sep_fiber(const SepFiberArgs<R> &a, cudaStream_t st) {
+    cudaError_t e = set_smem_once((const void *)k_sep_fiber<R>, a.smem);
+    if (e != cudaSuccess) return e;
+    const int64_t total = a.outer * a.inner;
+    const int64_t blocks = (total + a.threads - 1) / a.threads;
+    k_sep_fiber<R><<<(unsigned)blocks, a.threads, a.smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_sep_fiber<float>(const SepFiberArgs<float> &, cudaStream_t);
+template cudaError_t launch_sep_fiber<double>(const SepFiberArgs<double> &, cudaStream_t);
+
 }  // namespace tb
