@@ -220,8 +220,7 @@ def main():
     import paper_2411_03029_gb300 as tb
     tb.build.build()
     w = workload(args)
-    prec = args.precision if args.precision is not None else (
-        tb.PREC_C64 if w.precision == tb.PREC_C64_SPLITBF16 else w.precision)
+    prec = args.precision if args.precision is not None else w.precision
     mask = (1 << prec) | ((1 << tb.PREC_C128) if not args.no_fp64 else 0)
     op = tb.from_workload(w, precisions=mask, use_graphs=not args.profile_only, precision=prec)
     info = op.info()

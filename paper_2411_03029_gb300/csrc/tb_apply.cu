@@ -24,39 +24,113 @@
 namespace tb {
 
 constexpr int AP_THREADS = 256;
-constexpr int AB = 4;   // output rows per thread in a mode product
+constexpr int CORE_THREADS = 256;
+constexpr int AB = 4;   // output rows per thread in the leaf passes
 
-// dst[p][a][q] (=|+=) sum_b A[a][b] src[p][b][q]; A is o x m row-major in smem.
-template <class R>
-TB_DEV void mode_pass(const cx<R> *__restrict__ src, cx<R> *__restrict__ dst, const cx<R> *__restrict__ A,
-                      int pre, int mk, int ok, int post, bool acc) {
-    const int nab = (ok + AB - 1) / AB;
+// Staged factors are transposed: At[b * lda + a] = A[a][b] with lda = o rounded
+// up to a multiple of 4 and zero columns a >= o (see stage()).
+TB_HD int lda_of(int o) { return (o + 3) & ~3; }
+
+// dst[p][a][q] (=|+=) sum_b A[a][b] src[p][b][q] with A given transposed (At).
+// Each item computes NR consecutive output rows a of one column (p, q); items
+// run with q fastest, so a warp shares (p, a-block) whenever post >= 32 and its
+// reads of At are broadcasts.
+template <class R, int NR>
+TB_DEV void mode_pass_rows(const cx<R> *__restrict__ src, cx<R> *__restrict__ dst, const cx<R> *__restrict__ At,
+                           int pre, int mk, int ok, int post, bool acc) {
+    const int nab = (ok + NR - 1) / NR, lda = lda_of(ok);
     const int items = pre * nab * post;
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int q = it % post;
         const int r = it / post;
         const int ab = r % nab, p = r / nab;
-        const int a0 = ab * AB;
-        cx<R> c[AB];
+        const int a0 = ab * NR;
+        cx<R> c[NR];
 #pragma unroll
-        for (int i = 0; i < AB; ++i) c[i] = {R(0), R(0)};
+        for (int i = 0; i < NR; ++i) c[i] = {R(0), R(0)};
         const cx<R> *s = src + (p * mk) * post + q;
-        int arow[AB];
+        int acol[NR];
 #pragma unroll
-        for (int i = 0; i < AB; ++i) arow[i] = min(a0 + i, ok - 1) * mk;
+        for (int i = 0; i < NR; ++i) acol[i] = min(a0 + i, ok - 1);
+#pragma unroll 2
         for (int b = 0; b < mk; ++b) {
             const cx<R> x = s[b * post];
+            const cx<R> *arow = At + b * lda;
 #pragma unroll
-            for (int i = 0; i < AB; ++i) cmac(c[i], A[arow[i] + b], x);
+            for (int i = 0; i < NR; ++i) cmac(c[i], arow[acol[i]], x);
         }
 #pragma unroll
-        for (int i = 0; i < AB; ++i) {
+        for (int i = 0; i < NR; ++i) {
             if (a0 + i < ok) {
                 const int idx = (p * ok + a0 + i) * post + q;
                 dst[idx] = acc ? dst[idx] + c[i] : c[i];
             }
         }
     }
+}
+
+// Register-tiled form: each item computes 4 output rows x 2 adjacent columns
+// from the transposed factor At[b][a] (row stride lda, a multiple of 4, zero
+// padded), so one b step costs two vector loads of At, one vector load of the
+// column pair and 8 complex FMAs.  Needs post even.
+template <class R>
+TB_DEV void mode_pass_tile(const cx<R> *__restrict__ src, cx<R> *__restrict__ dst, const cx<R> *__restrict__ At,
+                           int lda, int pre, int mk, int ok, int post, bool acc) {
+    const int nab = (ok + 3) / 4, nqb = post >> 1;
+    const int items = pre * nab * nqb;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int qb = it % nqb;
+        const int r = it / nqb;
+        const int ab = r % nab, p = r / nab;
+        const int a0 = ab * 4, q = 2 * qb;
+        cx<R> c[4][2];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) c[i][0] = c[i][1] = {R(0), R(0)};
+        const cx<R> *s = src + (p * mk) * post + q;
+        const cx<R> *ap = At + a0;
+#pragma unroll 2
+        for (int b = 0; b < mk; ++b) {
+            const cx<R> x0 = s[b * post], x1 = s[b * post + 1];
+            const cx<R> *arow = ap + b * lda;
+            cx<R> av[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = arow[i];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                cmac(c[i][0], av[i], x0);
+                cmac(c[i][1], av[i], x1);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (a0 + i < ok) {
+                const int idx = (p * ok + a0 + i) * post + q;
+                if (acc) {
+                    dst[idx] = dst[idx] + c[i][0];
+                    dst[idx + 1] = dst[idx + 1] + c[i][1];
+                } else {
+                    dst[idx] = c[i][0];
+                    dst[idx + 1] = c[i][1];
+                }
+            }
+        }
+    }
+}
+
+// One mode product with the transposed factor At.  The register-tiled form is
+// used when the column count is even and there is an item for every thread;
+// otherwise the largest row block that still gives every thread an item.
+template <class R>
+TB_DEV void mode_pass(const cx<R> *__restrict__ src, cx<R> *__restrict__ dst, const cx<R> *__restrict__ At,
+                      int pre, int mk, int ok, int post, bool acc) {
+    const int cols = pre * post, T = blockDim.x;
+    if ((post & 1) == 0 && (cols / 2) * ((ok + 3) / 4) >= T) {
+        mode_pass_tile<R>(src, dst, At, lda_of(ok), pre, mk, ok, post, acc);
+        return;
+    }
+    if (cols * ((ok + 7) / 8) >= T) mode_pass_rows<R, 8>(src, dst, At, pre, mk, ok, post, acc);
+    else if (cols * ((ok + 3) / 4) >= T) mode_pass_rows<R, 4>(src, dst, At, pre, mk, ok, post, acc);
+    else mode_pass_rows<R, 2>(src, dst, At, pre, mk, ok, post, acc);
 }
 
 // Passes k0 .. k1-1 of Y = X x_0 A_0 x_1 A_1 ... x_{d-1} A_{d-1}; X dims m[],
@@ -106,13 +180,14 @@ TB_DEV void leaf_first_pass(int d, const int *m, const int *o, const cx<R> *A, c
         cx<R> c[AB];
 #pragma unroll
         for (int i = 0; i < AB; ++i) c[i] = {R(0), R(0)};
-        int arow[AB];
+        int acol[AB];
 #pragma unroll
-        for (int i = 0; i < AB; ++i) arow[i] = min(a0 + i, ok - 1) * mk;
+        for (int i = 0; i < AB; ++i) acol[i] = min(a0 + i, ok - 1);
+        const int lda = lda_of(ok);
         for (int b = 0; b < mk; ++b) {
             const cx<R> x = user[base + (int64_t)gt[0][b] * gstride[0] * nv];
 #pragma unroll
-            for (int i = 0; i < AB; ++i) cmac(c[i], A[arow[i] + b], x);
+            for (int i = 0; i < AB; ++i) cmac(c[i], A[b * lda + acol[i]], x);
         }
 #pragma unroll
         for (int i = 0; i < AB; ++i)
@@ -136,7 +211,8 @@ TB_DEV void leaf_last_pass(int d, const int *m, const int *o, const cx<R> *A, co
         const int a = r % ok, p = r / ok;
         cx<R> c = {R(0), R(0)};
         const cx<R> *s = src + p * mk * post + v;
-        for (int b = 0; b < mk; ++b) cmac(c, A[a * mk + b], s[b * post]);
+        const int lda = lda_of(ok);
+        for (int b = 0; b < mk; ++b) cmac(c, A[b * lda + a], s[b * post]);
         int64_t addr = (int64_t)gt[k][a] * gstride[k];
         int rp = p;
         for (int i = k - 1; i >= 0; --i) {
@@ -182,23 +258,25 @@ ChainSmem chain_smem(int d, const int *m, const int *o, int64_t nvc) {
         if (k & 1) s.b1 = s.b1 > t ? s.b1 : t;
         else s.b0 = s.b0 > t ? s.b0 : t;
     }
-    for (int k = 0; k < d; ++k) s.a += (int64_t)m[k] * o[k];
+    for (int k = 0; k < d; ++k) s.a += (int64_t)m[k] * lda_of(o[k]);
     return s;
 }
 
-// Copy an r x c row-major block into shared memory as A (o = r, m = c) or as
-// A^T (o = c, m = r), optionally conjugated.
+// Stage an r x c row-major factor block for a mode product that applies
+// op(A) = A (o = r, m = c) or A^T (o = c, m = r), optionally conjugated, in
+// the transposed layout dst[b * lda + a] = op(A)[a][b], lda = lda_of(o), with
+// zero columns a in [o, lda).
 template <class R>
 TB_DEV void stage(cx<R> *dst, const cx<R> *__restrict__ src, int r, int c, bool trans, bool cj) {
-    const int n = r * c;
-    for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        cx<R> v = src[e];
-        if (cj) v.y = -v.y;
-        if (!trans) dst[e] = v;
-        else {
-            const int i = e / c, j = e - i * c;
-            dst[j * r + i] = v;
+    const int o = trans ? c : r, m = trans ? r : c, lda = lda_of(o);
+    for (int e = threadIdx.x; e < m * lda; e += blockDim.x) {
+        const int b = e / lda, a = e - b * lda;
+        cx<R> v = {R(0), R(0)};
+        if (a < o) {
+            v = trans ? src[b * c + a] : src[a * c + b];
+            if (cj) v.y = -v.y;
         }
+        dst[e] = v;
     }
 }
 
@@ -222,7 +300,7 @@ TB_DEV const cx<R> *fac_block(const FacRef<R> &f, int k, int64_t F, int64_t M, i
 
 // ------------------------------------------------------------------ level pass
 template <class R, Pass PASS, bool CONJ>
-__global__ void __launch_bounds__(AP_THREADS) k_level(const LevelArgs<R> a) {
+__global__ void __launch_bounds__(AP_THREADS, 2) k_level(const LevelArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
     cx<R> *X = sm + a.offX, *B0 = sm + a.offB0, *B1 = sm + a.offB1, *Y = sm + a.offY, *Asm = sm + a.offA;
@@ -245,10 +323,14 @@ __global__ void __launch_bounds__(AP_THREADS) k_level(const LevelArgs<R> a) {
 
     cx<R> *As[MAXD];
     {
+        // staged factors: m x lda_of(o), with the factor block applied as is
+        // (LeafIn, Split) or transposed (LeafOut, Gather)
+        const bool tr = (PASS == Pass::LeafOut || PASS == Pass::Gather);
         int off = 0;
         for (int k = 0; k < d; ++k) {
             As[k] = Asm + off;
-            off += a.fac.rows[k] * a.fac.cols[k];
+            const int ro = tr ? a.fac.cols[k] : a.fac.rows[k], rm = tr ? a.fac.rows[k] : a.fac.cols[k];
+            off += rm * lda_of(ro);
         }
     }
 
@@ -409,7 +491,7 @@ cudaError_t launch_level(Pass pass, bool conj, const LevelArgs<R> &a, cudaStream
 // Forward: G_{t,s}[a] = sum_b C[a][b] F_{t,s}[b] on compact core indices; a warp
 // per core row, lanes over b, warp-shuffle reduction.  Adjoint: thread per b.
 template <class R, int NVC>
-__global__ void __launch_bounds__(AP_THREADS) k_core_dense(const CoreApplyArgs<R> a, int adjoint) {
+__global__ void __launch_bounds__(CORE_THREADS) k_core_dense(const CoreApplyArgs<R> a, int adjoint) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<R> *Xc = reinterpret_cast<cx<R> *>(smraw);
     const int d = a.d;
@@ -513,7 +595,7 @@ cudaError_t launch_core_dense(bool adjoint, const CoreApplyArgs<R> &a, cudaStrea
     else fn = k_core_dense<R, 16>;
     cudaError_t e = set_smem_once((const void *)fn, a.smem);
     if (e != cudaSuccess) return e;
-    fn<<<grid, AP_THREADS, a.smem, st>>>(a, adjoint ? 1 : 0);
+    fn<<<grid, CORE_THREADS, a.smem, st>>>(a, adjoint ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -521,7 +603,7 @@ cudaError_t launch_core_dense(bool adjoint, const CoreApplyArgs<R> &a, cudaStrea
 // For a kernel that is a product over modes, K(t-bar, s-bar) = kron_k K_k and the
 // core contraction is a mode-product chain with the per-mode factors.
 template <class R, bool ADJ>
-__global__ void __launch_bounds__(AP_THREADS) k_core_kron(const CoreApplyArgs<R> a) {
+__global__ void __launch_bounds__(CORE_THREADS) k_core_kron(const CoreApplyArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
     cx<R> *X = sm + a.offX, *B0 = sm + a.offB0, *B1 = sm + a.offB1, *Y = sm + a.offY, *Asm = sm + a.offA;
@@ -540,7 +622,7 @@ __global__ void __launch_bounds__(AP_THREADS) k_core_kron(const CoreApplyArgs<R>
         m[k] = ADJ ? a.Rt[k] : a.Rs[k];
         o[k] = ADJ ? a.Rs[k] : a.Rt[k];
         As[k] = Asm + off;
-        off += a.Rt[k] * a.Rs[k];
+        off += m[k] * lda_of(o[k]);
         const int64_t tk = (t >> (a.Lc * (d - 1 - k))) & (nb - 1), sk = (s >> (a.Lc * (d - 1 - k))) & (nb - 1);
         stage<R>(As[k], a.kron[k] + (tk * nb + sk) * a.Rt[k] * a.Rs[k], a.Rt[k], a.Rs[k], ADJ, ADJ);
     }
@@ -565,7 +647,7 @@ cudaError_t launch_core_kron(bool adjoint, const CoreApplyArgs<R> &a, cudaStream
     void (*fn)(const CoreApplyArgs<R>) = adjoint ? k_core_kron<R, true> : k_core_kron<R, false>;
     cudaError_t e = set_smem_once((const void *)fn, a.smem);
     if (e != cudaSuccess) return e;
-    fn<<<grid, AP_THREADS, a.smem, st>>>(a);
+    fn<<<grid, CORE_THREADS, a.smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -261,15 +261,38 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
         cp = next(cp);
     }
 
+    // the two (k, v) input values this thread converts for a chunk; loaded one
+    // chunk ahead so their L2 latency overlaps the previous chunk's work
+    constexpr int PER = KC * 16 / THREADS;
+    auto load_x = [&](Cursor c, cx<float> *x) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) x[i] = cx<float>{0.f, 0.f};
+        if (c.item >= a.nitems) return;
+        const int pp = a.items[c.item].pair;
+        int r[MAXD], M = 1;
+        for (int k = 0; k < d; ++k) {
+            r[k] = a.dims[(int64_t)pp * 2 * d + (a.adjoint ? k : d + k)];
+            M *= r[k];
+        }
+        const cx<float> *xin = a.in + (int64_t)pp * a.in_tsize * a.nv;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int e = tid + i * THREADS;
+            const int v = e & 15, k = c.kc * KC + (e >> 4);
+            if (v < a.nvc && k < M)
+                x[i] = xin[(int64_t)compact_to_padded(k, d, r, a.in_R) * a.nv + a.v0 + v];
+        }
+    };
+    cx<float> xcur[PER], xnxt[PER];
+    load_x(cm, xcur);
+
     while (ok && cm.item < a.nitems) {
         const CoreItem it = a.items[cm.item];
         const int p = it.pair;
-        int rin[MAXD], rout[MAXD];
-        int Min = 1, Mout = 1;
+        int rout[MAXD];
+        int Mout = 1;
         for (int k = 0; k < d; ++k) {
-            rin[k] = a.dims[(int64_t)p * 2 * d + (a.adjoint ? k : d + k)];
             rout[k] = a.dims[(int64_t)p * 2 * d + (a.adjoint ? d + k : k)];
-            Min *= rin[k];
             Mout *= rout[k];
         }
         const int s = (int)(g % STAGES);
@@ -280,19 +303,14 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
             cp = next(cp);
         }
         if (__syncthreads_or(!ok)) { ok = false; break; }
+        load_x(next(cm), xnxt);
         // build A for this chunk: rows v / 16+v (x_hi re/im), 32+v / 48+v (x_lo)
         unsigned char *A = sm + s * STAGE_BYTES;
-        const cx<float> *xin = a.in + (int64_t)p * a.in_tsize * a.nv;
-        for (int e = tid; e < KC * 16; e += THREADS) {
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int e = tid + i * THREADS;
             const int v = e & 15, kk = e >> 4;
-            const int k = cm.kc * KC + kk;
-            float xr = 0.f, xi = 0.f;
-            if (v < a.nvc && k < Min) {
-                const int pos = compact_to_padded(k, d, rin, a.in_R);
-                const cx<float> x = xin[(int64_t)pos * a.nv + a.v0 + v];
-                xr = x.x;
-                xi = x.y;
-            }
+            const float xr = xcur[i].x, xi = xcur[i].y;
             const float hr = __bfloat162float(__float2bfloat16_rn(xr));
             const float hi = __bfloat162float(__float2bfloat16_rn(xi));
             const float lr = xr - hr, li = xi - hi;
@@ -323,6 +341,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
         const int64_t gdone = g;
         ++g;
         cm = next(cm);
+#pragma unroll
+        for (int i = 0; i < PER; ++i) xcur[i] = xnxt[i];
         if (!last) continue;
 
         // ------------------------------------------------------- epilogue
