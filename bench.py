@@ -54,7 +54,12 @@ def parse():
 
 def workload(args):
     w = W.WORKLOADS[args.workload]
-    return W.small(args.workload, args.n, nv=w.nv) if args.n else w
+    if not args.n:
+        return w
+    kw = {}
+    if w.kind == W.HELMHOLTZ:   # keep the points per wavelength of the full workload
+        kw["params"] = (w.params[0] * args.n / w.n,)
+    return W.small(args.workload, args.n, nv=w.nv, **kw)
 
 
 def dist_init():
