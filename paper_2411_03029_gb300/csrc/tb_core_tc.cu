@@ -4,27 +4,40 @@
 //
 // Real form.  With the core stored as interleaved (re, im) pairs, a core row
 // is a real row of length 2 M_s, and for each RHS v the two real rows
-//     A_re[v] = ( Re x_k, -Im x_k )_k      A_im[v] = ( Im x_k, Re x_k )_k
-// give Re G[n][v] = <C_row n, A_re[v]> and Im G[n][v] = <C_row n, A_im[v]>.
-// So G^T = A (M x 2Ms) * C^T with M = 2 nv, a tensor-core product
-// D[m][n] = sum_k A[m][k] B[n][k] whose B operand is the core itself, K-major.
+//     B_re[v] = ( Re x_k, -Im x_k )_k      B_im[v] = ( Im x_k, Re x_k )_k
+// give Re G[n][v] = <C_row n, B_re[v]> and Im G[n][v] = <C_row n, B_im[v]>.
+// So G = C B^T, a tensor-core product D[m][n] = sum_k A[m][k] B[n][k] whose A
+// operand is a tile of up to 128 core rows (K-major, MMA M = 128) and whose B
+// operand holds 64 rows: B_re, B_im of x_hi (rows 0..31) and of x_lo (32..63)
+// for 16 right-hand sides (MMA N = 64).
 //
 // Split BF16.  C = Ch + Cl and x = xh + xl in BF16 (hi = rn(v), lo = rn(v - hi)).
-// A holds the rows of xh (rows 0..31) and xl (rows 32..63); two products with
-// B = Ch and B = Cl land in two TMEM accumulators, and the four partial
-// products xh Ch + xl Ch + xh Cl + xl Cl are summed in FP32 in the epilogue.
+// The products Ch B^T and Cl B^T land in two 64-column TMEM accumulators and
+// the epilogue sums the four partial products xh Ch + xl Ch + xh Cl + xl Cl in
+// FP32.
 //
 // Core storage (built once by k_core_tile): per pair, row tiles of up to 128
 // core rows (rows padded to 16) and K-chunks of 32 complex columns (columns
 // padded to 32).  Each (tile, chunk) block holds rows x 128 B of Ch followed by
-// rows x 128 B of Cl, in the 128-byte-swizzled layout the MMA reads from
-// shared memory, so one bulk copy moves a block.
+// rows x 128 B of Cl, in the 128-byte-swizzled K-major layout the MMA reads
+// from shared memory, so one bulk copy moves a block.
 //
-// Pipeline.  One 256-thread block per SM walks its work items (pair, row
-// tile); K-chunks stream through 4 shared-memory stages with bulk copies
-// issued two chunks ahead.  Every wait on an mbarrier is bounded: on expiry
-// the block records TB_ETIMEOUT in the error word, drains its outstanding
-// copies (again bounded), frees its tensor memory and returns.
+// Pipeline.  One 384-thread block per SM walks its work items (pair, row tile)
+// with warp-specialised roles that meet at mbarriers:
+//   warp 0       streams the core K-chunks into STAGES shared-memory stages
+//                (cp.async.bulk, completion counted in bytes);
+//   warps 8..11  load the matching 32 x 16 input values (three chunks ahead),
+//                split them into BF16 pairs and write the B rows of the stage;
+//   warp 1       issues the MMAs of a chunk once both halves of its stage have
+//                landed and releases the stage with tcgen05.commit;
+//   warps 4..7   drain a finished item's accumulator from tensor memory and
+//                write its rows of G.  Accumulators are double-buffered, so
+//                the next item's MMAs overlap the drain;
+//   warps 2..3   zero the padded entries of each pair's output tile.
+// Every mbarrier wait is bounded.  A role whose wait expires records
+// TB_ETIMEOUT and raises a block-wide abort flag that ends the other roles'
+// waits; the block then waits, again bounded, for its copies and MMAs in
+// flight, frees its tensor memory and returns.
 #include <cuda_bf16.h>
 
 #include "tb_kernels.cuh"
@@ -33,17 +46,21 @@ namespace tb {
 
 namespace tc {
 
-constexpr int NT = 128;             // core rows per work item (MMA N)
-constexpr int KC = 32;              // complex core columns per K-chunk (64 BF16 = 128 B)
-constexpr int STAGES = 4;
-constexpr int AHEAD = 2;            // chunks prefetched ahead of the MMA
-constexpr int THREADS = 256;
-constexpr int A_BYTES = 128 * 128;  // 128 rows x 128 B
-constexpr int B_BYTES = 2 * NT * 128;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int EPI_BYTES = 32 * NT * 4;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + EPI_BYTES + 1024;
-constexpr uint32_t TMEM_COLS = 2 * NT;   // D_hi at [0, NT), D_lo at [NT, 2 NT)
+constexpr int NT = 128;                    // core rows per work item (MMA M)
+constexpr int KC = 32;                     // complex core columns per K-chunk (64 BF16 = 128 B)
+constexpr int NB = 64;                     // B rows (MMA N)
+constexpr int STAGES = 5;
+constexpr int THREADS = 384;
+constexpr int CORE_BYTES = 2 * NT * 128;   // Ch tile then Cl tile
+constexpr int X_BYTES = NB * 128;
+constexpr int STAGE_BYTES = CORE_BYTES + X_BYTES;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr uint32_t ACC_COLS = 128;         // D_h at [0, 64), D_l at [64, 128)
+constexpr uint32_t TMEM_COLS = 2 * ACC_COLS;
+constexpr int EPI_WARP0 = 4;               // warps 4..7: one per TMEM lane quarter
+constexpr int CONV_WARP0 = 8;              // warps 8..11
+constexpr int PAD_WARP0 = 2;               // warps 2..3
+constexpr int NEPI = 128, NCONV = 128, NPAD = 64;
 constexpr long long SPIN_LIMIT = 1ll << 26;
 
 TB_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -55,6 +72,9 @@ TB_DEV void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
+TB_DEV void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 TB_DEV bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
     uint32_t ok;
     asm volatile(
@@ -64,10 +84,13 @@ TB_DEV bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false if the barrier phase did not complete within the limit.
-TB_DEV bool mbar_wait(uint64_t *bar, uint32_t phase) {
-    for (long long i = 0; i < SPIN_LIMIT; ++i)
+// Bounded wait: false if the phase did not complete within the limit, or (when
+// `abort` is given) once another role of the block has given up.
+TB_DEV bool mbar_wait(uint64_t *bar, uint32_t phase, const volatile int *abort = nullptr) {
+    for (long long i = 0; i < SPIN_LIMIT; ++i) {
         if (mbar_try_wait(bar, phase)) return true;
+        if (abort && (i & 255) == 255 && *abort) return false;
+    }
     return false;
 }
 TB_DEV void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -106,17 +129,21 @@ TB_DEV void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                  : "memory");
 }
-TB_DEV void tmem_ld16(uint32_t taddr, float *v) {
-    uint32_t r[16];
+// 32 consecutive accumulator columns of this warp's 32 TMEM lanes (one per thread)
+TB_DEV void tmem_ld32(uint32_t taddr, float *v) {
+    uint32_t r[32];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr)
         : "memory");
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // byte offset of (row, byte-in-row) in a 128 B-swizzled K-major tile
@@ -196,26 +223,31 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
     using namespace tc;
     extern __shared__ unsigned char tc_smem_raw[];
     unsigned char *sm = (unsigned char *)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full_bar[STAGES], mma_bar[STAGES];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], xfull_bar[STAGES], empty_bar[STAGES];
+    __shared__ __align__(8) uint64_t accf_bar[2], acce_bar[2], done_bar;
     __shared__ uint32_t tmem_base_sh;
     __shared__ int abort_sh;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int d = a.d;
-    float *epi = reinterpret_cast<float *>(sm + STAGES * STAGE_BYTES);
+    const volatile int *abort = &abort_sh;
+    auto give_up = [&]() {
+        if (atomicExch(&abort_sh, 1) == 0) atomicExch(a.err, (int)TB_ETIMEOUT);
+    };
 
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
-            mbar_init(&mma_bar[s], 1);
+            mbar_init(&xfull_bar[s], NCONV);
+            mbar_init(&empty_bar[s], 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf_bar[b], 1);
+            mbar_init(&acce_bar[b], NEPI);
+        }
+        mbar_init(&done_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_sh = 0;
     }
-    // A rows 64..127 stay zero; rows 0..63 are rewritten for every chunk
-    for (int s = 0; s < STAGES; ++s)
-        for (int i = tid; i < A_BYTES / 16; i += THREADS)
-            reinterpret_cast<uint4 *>(sm + s * STAGE_BYTES)[i] = make_uint4(0, 0, 0, 0);
-    fence_proxy_async();
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_sh)),
@@ -227,182 +259,263 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
+    int64_t issued = 0;   // producer: chunks whose copy was issued
 
-    // chunk streams: "copy" runs AHEAD chunks in front of "compute"
-    struct Cursor {
-        int64_t item;
-        int kc;
-    };
-    auto next = [&](Cursor c) {
-        if (++c.kc >= a.items[c.item].nkc) {
-            c.kc = 0;
-            c.item += gridDim.x;
-        }
-        return c;
-    };
-    Cursor cp{(int64_t)blockIdx.x, 0}, cm{(int64_t)blockIdx.x, 0};
-    int64_t g_copy = 0, g = 0;   // chunks issued / computed by this block
-    bool ok = true;
-    auto issue = [&](Cursor c, int64_t gi) {
-        // stage reuse: MMAs of chunk gi - STAGES must have drained it
-        const int s = (int)(gi % STAGES);
-        if (gi >= STAGES && !mbar_wait(&mma_bar[s], (uint32_t)(((gi - STAGES) / STAGES) & 1))) return false;
-        if (tid == 0) {
-            const CoreItem it = a.items[c.item];
-            const uint32_t bytes = (uint32_t)it.rows * 256u;
-            mbar_expect_tx(&full_bar[s], bytes);
-            bulk_g2s(sm + s * STAGE_BYTES + A_BYTES, a.tiles + it.boff + (int64_t)c.kc * bytes, bytes, &full_bar[s]);
-        }
-        return true;
-    };
-    for (int i = 0; i < AHEAD && cp.item < a.nitems && ok; ++i) {
-        ok = issue(cp, g_copy);
-        ++g_copy;
-        cp = next(cp);
-    }
-
-    // the two (k, v) input values this thread converts for a chunk; loaded one
-    // chunk ahead so their L2 latency overlaps the previous chunk's work
-    constexpr int PER = KC * 16 / THREADS;
-    auto load_x = [&](Cursor c, cx<float> *x) {
-#pragma unroll
-        for (int i = 0; i < PER; ++i) x[i] = cx<float>{0.f, 0.f};
-        if (c.item >= a.nitems) return;
-        const int pp = a.items[c.item].pair;
-        int r[MAXD], M = 1;
-        for (int k = 0; k < d; ++k) {
-            r[k] = a.dims[(int64_t)pp * 2 * d + (a.adjoint ? k : d + k)];
-            M *= r[k];
-        }
-        const cx<float> *xin = a.in + (int64_t)pp * a.in_tsize * a.nv;
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int e = tid + i * THREADS;
-            const int v = e & 15, k = c.kc * KC + (e >> 4);
-            if (v < a.nvc && k < M)
-                x[i] = xin[(int64_t)compact_to_padded(k, d, r, a.in_R) * a.nv + a.v0 + v];
-        }
-    };
-    cx<float> xcur[PER], xnxt[PER];
-    load_x(cm, xcur);
-
-    while (ok && cm.item < a.nitems) {
-        const CoreItem it = a.items[cm.item];
-        const int p = it.pair;
-        int rout[MAXD];
-        int Mout = 1;
-        for (int k = 0; k < d; ++k) {
-            rout[k] = a.dims[(int64_t)p * 2 * d + (a.adjoint ? d + k : k)];
-            Mout *= rout[k];
-        }
-        const int s = (int)(g % STAGES);
-        // prefetch
-        if (cp.item < a.nitems) {
-            ok = issue(cp, g_copy);
-            ++g_copy;
-            cp = next(cp);
-        }
-        if (__syncthreads_or(!ok)) { ok = false; break; }
-        load_x(next(cm), xnxt);
-        // build A for this chunk: rows v / 16+v (x_hi re/im), 32+v / 48+v (x_lo)
-        unsigned char *A = sm + s * STAGE_BYTES;
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int e = tid + i * THREADS;
-            const int v = e & 15, kk = e >> 4;
-            const float xr = xcur[i].x, xi = xcur[i].y;
-            const float hr = __bfloat162float(__float2bfloat16_rn(xr));
-            const float hi = __bfloat162float(__float2bfloat16_rn(xi));
-            const float lr = xr - hr, li = xi - hi;
-            const uint32_t b = 4u * kk;
-            *reinterpret_cast<uint32_t *>(A + swz(v, b)) = pack_bf16(hr, -hi);
-            *reinterpret_cast<uint32_t *>(A + swz(16 + v, b)) = pack_bf16(hi, hr);
-            *reinterpret_cast<uint32_t *>(A + swz(32 + v, b)) = pack_bf16(lr, -li);
-            *reinterpret_cast<uint32_t *>(A + swz(48 + v, b)) = pack_bf16(li, lr);
-        }
-        fence_proxy_async();
-        __syncthreads();
-        ok = mbar_wait(&full_bar[s], (uint32_t)((g / STAGES) & 1));
-        if (__syncthreads_or(!ok)) { ok = false; break; }
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t ab = smem_u32(A), bh = ab + A_BYTES, bl = bh + (uint32_t)it.rows * 128u;
-            const uint32_t idesc = idesc_bf16(it.rows);
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-                const uint32_t acc = (cm.kc > 0 || ks > 0) ? 1u : 0u;
-                const uint32_t koff = 32u * ks;
-                mma_bf16(tmem, sdesc(ab + koff), sdesc(bh + koff), idesc, acc);
-                mma_bf16(tmem + NT, sdesc(ab + koff), sdesc(bl + koff), idesc, acc);
-            }
-            mma_commit(&mma_bar[s]);
-        }
-        const bool last = (cm.kc + 1 == it.nkc);
-        const int64_t gdone = g;
-        ++g;
-        cm = next(cm);
-#pragma unroll
-        for (int i = 0; i < PER; ++i) xcur[i] = xnxt[i];
-        if (!last) continue;
-
-        // ------------------------------------------------------- epilogue
-        ok = mbar_wait(&mma_bar[s], (uint32_t)((gdone / STAGES) & 1));
-        if (__syncthreads_or(!ok)) { ok = false; break; }
-        tc_fence_after();
-        const int wq = warp & 3;   // TMEM lane quarter this warp may read
-        const int ngrp = it.rows / 16;
-        // pass 1: lanes 32..63 (x_lo rows) -> epi; pass 2: lanes 0..31 add
-        for (int pass = 0; pass < 2; ++pass) {
-            if (wq == 1 - pass) {
-                for (int gq = (warp >> 2); gq < ngrp; gq += 2) {
-                    float dh[16], dl[16];
-                    const uint32_t taddr = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(16 * gq);
-                    tmem_ld16(taddr, dh);
-                    tmem_ld16(taddr + NT, dl);
-                    float *row = epi + lane * NT + 16 * gq;
-#pragma unroll
-                    for (int c = 0; c < 16; ++c) row[c] = (pass == 0) ? dh[c] + dl[c] : row[c] + dh[c] + dl[c];
+    if (warp == 0) {
+        // ------------------------------------------------ core chunk producer
+        if (lane == 0) {
+            bool ok = true;
+            for (int64_t item = blockIdx.x; ok && item < a.nitems; item += gridDim.x) {
+                const CoreItem it = a.items[item];
+                const uint32_t bytes = (uint32_t)it.rows * 256u;
+                const unsigned char *src = a.tiles + it.boff;
+                for (int kc = 0; kc < it.nkc; ++kc) {
+                    const int s = (int)(issued % STAGES);
+                    if (issued >= STAGES &&
+                        !mbar_wait(&empty_bar[s], (uint32_t)((issued / STAGES - 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(&full_bar[s], bytes);
+                    bulk_g2s(sm + s * STAGE_BYTES, src + (int64_t)kc * bytes, bytes, &full_bar[s]);
+                    ++issued;
                 }
+            }
+            if (!ok) give_up();
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            int64_t gi = 0, ni = 0;
+            bool ok = true;
+            const uint32_t idesc = idesc_bf16(NB);
+            for (int64_t item = blockIdx.x; ok && item < a.nitems; item += gridDim.x, ++ni) {
+                const CoreItem it = a.items[item];
+                const int b = (int)(ni & 1);
+                if (ni >= 2 && !mbar_wait(&acce_bar[b], (uint32_t)(((ni >> 1) - 1) & 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t dh = tmem + (uint32_t)b * ACC_COLS, dl = dh + 64u;
+                for (int kc = 0; kc < it.nkc; ++kc, ++gi) {
+                    const int s = (int)(gi % STAGES);
+                    const uint32_t ph = (uint32_t)((gi / STAGES) & 1);
+                    if (!mbar_wait(&full_bar[s], ph, abort) || !mbar_wait(&xfull_bar[s], ph, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t ch = smem_u32(sm + s * STAGE_BYTES);
+                    const uint32_t cl = ch + (uint32_t)it.rows * 128u, xb = ch + CORE_BYTES;
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint32_t acc = (kc > 0 || ks > 0) ? 1u : 0u;
+                        const uint32_t koff = 32u * ks;
+                        mma_bf16(dh, sdesc(ch + koff), sdesc(xb + koff), idesc, acc);
+                        mma_bf16(dl, sdesc(cl + koff), sdesc(xb + koff), idesc, acc);
+                    }
+                    mma_commit(&empty_bar[s]);
+                }
+                if (!ok) break;
+                mma_commit(&accf_bar[b]);
+            }
+            if (!ok) give_up();
+            // completes once every MMA issued above has finished
+            mma_commit(&done_bar);
+            mbar_wait(&done_bar, 0);
+        }
+    } else if (warp >= CONV_WARP0) {
+        // ------------------------------------------- input split into BF16 rows
+        const int t = tid - CONV_WARP0 * 32;
+        const int kl = t >> 2, vq = (t & 3) * 4;   // column kl of the chunk, RHS vq .. vq+3
+        // look-ahead cursor: the next chunk whose input values are loaded, with
+        // the metadata of its item (read once per item)
+        int64_t litem = blockIdx.x;
+        int lkc = 0, lnkc = 0, lM = 0;
+        int lr[MAXD];
+        const cx<float> *lbase = a.in;
+        auto meta = [&]() {
+            if (litem >= a.nitems) return;
+            const CoreItem it = a.items[litem];
+            lnkc = it.nkc;
+            lM = 1;
+            for (int k = 0; k < d; ++k) {
+                lr[k] = a.dims[(int64_t)it.pair * 2 * d + (a.adjoint ? k : d + k)];
+                lM *= lr[k];
+            }
+            lbase = a.in + (int64_t)it.pair * a.in_tsize * a.nv + a.v0 + vq;
+        };
+        const bool vec = (a.nv & 1) == 0 && vq + 4 <= a.nvc;   // two aligned 16-byte loads
+        auto load_next = [&](cx<float> *x) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) x[i] = cx<float>{0.f, 0.f};
+            if (litem >= a.nitems) return;
+            const int k = lkc * KC + kl;
+            if (k < lM) {
+                const cx<float> *src = lbase + (int64_t)compact_to_padded(k, d, lr, a.in_R) * a.nv;
+                if (vec) {
+                    const float4 u = *reinterpret_cast<const float4 *>(src);
+                    const float4 w = *reinterpret_cast<const float4 *>(src + 2);
+                    x[0] = cx<float>{u.x, u.y};
+                    x[1] = cx<float>{u.z, u.w};
+                    x[2] = cx<float>{w.x, w.y};
+                    x[3] = cx<float>{w.z, w.w};
+                } else {
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        if (vq + i < a.nvc) x[i] = src[i];
+                }
+            }
+            if (++lkc >= lnkc) {
+                lkc = 0;
+                litem += gridDim.x;
+                meta();
+            }
+        };
+        meta();
+        // three chunks of values in flight, in fixed registers (no copies of
+        // values that may still be loading)
+        cx<float> b0[4], b1[4], b2[4];
+        load_next(b0);
+        load_next(b1);
+        load_next(b2);
+        int64_t item = blockIdx.x, gi = 0;
+        int kc = 0, nkc = item < a.nitems ? a.items[item].nkc : 0;
+        bool ok = true;
+        auto step = [&](cx<float> *x) -> bool {
+            if (item >= a.nitems) return false;
+            const int s = (int)(gi % STAGES);
+            if (gi >= STAGES && !mbar_wait(&empty_bar[s], (uint32_t)((gi / STAGES - 1) & 1), abort)) {
+                ok = false;
+                return false;
+            }
+            unsigned char *X = sm + s * STAGE_BYTES + CORE_BYTES;
+            const uint32_t bo = 4u * kl;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int v = vq + i;
+                const float xr = x[i].x, xi = x[i].y;
+                const float hr = __bfloat162float(__float2bfloat16_rn(xr));
+                const float hi = __bfloat162float(__float2bfloat16_rn(xi));
+                const float lr_ = xr - hr, li = xi - hi;
+                *reinterpret_cast<uint32_t *>(X + swz(v, bo)) = pack_bf16(hr, -hi);
+                *reinterpret_cast<uint32_t *>(X + swz(16 + v, bo)) = pack_bf16(hi, hr);
+                *reinterpret_cast<uint32_t *>(X + swz(32 + v, bo)) = pack_bf16(lr_, -li);
+                *reinterpret_cast<uint32_t *>(X + swz(48 + v, bo)) = pack_bf16(li, lr_);
+            }
+            fence_proxy_async();   // generic-proxy writes -> visible to the MMA
+            mbar_arrive(&xfull_bar[s]);
+            ++gi;
+            load_next(x);   // the chunk three ahead
+            if (++kc >= nkc) {
+                kc = 0;
+                item += gridDim.x;
+                if (item < a.nitems) nkc = a.items[item].nkc;
+            }
+            return true;
+        };
+        while (step(b0) && step(b1) && step(b2)) {
+        }
+        if (!ok) give_up();
+    } else if (warp >= EPI_WARP0) {
+        // --------------------------------------------------------- epilogue
+        const int q = warp & 3;   // the TMEM lane quarter this warp may read
+        const int et = tid - EPI_WARP0 * 32;
+        int64_t ni = 0;
+        for (int64_t item = blockIdx.x; item < a.nitems; item += gridDim.x, ++ni) {
+            const CoreItem it = a.items[item];
+            const int b = (int)(ni & 1);
+            // warp-uniform outcome: the TMEM loads below are warp-collective
+            if (!__all_sync(0xffffffffu, mbar_wait(&accf_bar[b], (uint32_t)((ni >> 1) & 1), abort))) {
+                give_up();
+                break;
+            }
+            tc_fence_after();
+            float re[16], im[16], c[32];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)b * ACC_COLS;
+            tmem_ld32(taddr, c);   // Ch against the x_hi rows
+#pragma unroll
+            for (int v = 0; v < 16; ++v) { re[v] = c[v]; im[v] = c[16 + v]; }
+#pragma unroll
+            for (int part = 1; part < 4; ++part) {   // Ch x_lo, Cl x_hi, Cl x_lo
+                tmem_ld32(taddr + 32u * part, c);
+#pragma unroll
+                for (int v = 0; v < 16; ++v) { re[v] += c[v]; im[v] += c[16 + v]; }
             }
             tc_fence_before();
-            __syncthreads();
-        }
-        // write G rows of this tile: G[n][v] = epi[v][n] + i epi[16+v][n]
-        cx<float> *out = a.out + (int64_t)p * a.out_tsize * a.nv;
-        const int nbase = it.tile * NT;
-        for (int e = tid; e < it.rows * 16; e += THREADS) {
-            const int v = e & 15, nl = e >> 4;
-            const int n = nbase + nl;
-            if (v < a.nvc && n < Mout) {
+            mbar_arrive(&acce_bar[b]);
+
+            const int p = it.pair;
+            int rout[MAXD], Mout = 1;
+            for (int k = 0; k < d; ++k) {
+                rout[k] = a.dims[(int64_t)p * 2 * d + (a.adjoint ? d + k : k)];
+                Mout *= rout[k];
+            }
+            cx<float> *out = a.out + (int64_t)p * a.out_tsize * a.nv;
+            const int nl = 32 * q + lane, n = it.tile * NT + nl;
+            if (nl < it.rows && n < Mout) {
                 const int pos = compact_to_padded(n, d, rout, a.out_R);
-                out[(int64_t)pos * a.nv + a.v0 + v] = cx<float>{epi[v * NT + nl], epi[(16 + v) * NT + nl]};
-            }
-        }
-        if (it.tile == 0) {   // zero the padded entries no compact index reaches
-            for (int64_t e = tid; e < (int64_t)a.out_tsize * a.nvc; e += THREADS) {
-                int b = (int)(e / a.nvc), pad = 0;
-                const int v = (int)(e - (int64_t)b * a.nvc);
-                const int64_t idx = (int64_t)b * a.nv + a.v0 + v;
-                for (int k = d - 1; k >= 0; --k) {
-                    if (b % a.out_R[k] >= rout[k]) pad = 1;
-                    b /= a.out_R[k];
+                cx<float> *o = out + (int64_t)pos * a.nv + a.v0;
+                if ((a.nv & 1) == 0 && (a.v0 & 1) == 0) {   // 16-byte aligned pairs
+#pragma unroll
+                    for (int v = 0; v < 16; v += 2) {
+                        if (v + 1 < a.nvc)
+                            *reinterpret_cast<float4 *>(o + v) = make_float4(re[v], im[v], re[v + 1], im[v + 1]);
+                        else if (v < a.nvc)
+                            o[v] = cx<float>{re[v], im[v]};
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < 16; ++v)
+                        if (v < a.nvc) o[v] = cx<float>{re[v], im[v]};
                 }
-                if (pad) out[idx] = cx<float>{0.f, 0.f};
             }
         }
-        __syncthreads();
+    } else if (warp >= PAD_WARP0) {
+        // ------------------------------ zero the padded entries of the output
+        // A pair's output tile has padded R_k positions in every mode; the
+        // compact entries (index < r_k in every mode) are written by the
+        // epilogue, the rest must read as zero.  This role walks the block's
+        // items with tile 0 (one per pair) and clears the others, one 16-RHS
+        // run per entry, independently of the MMA pipeline.
+        const int pt = tid - PAD_WARP0 * 32;
+        int inner = 1;
+        for (int k = 1; k < d; ++k) inner *= a.out_R[k];
+        const bool vec = (a.nv & 1) == 0;
+        for (int64_t item = blockIdx.x; item < a.nitems && !*abort; item += gridDim.x) {
+            const CoreItem it = a.items[item];
+            if (it.tile != 0) continue;
+            int rout[MAXD];
+            for (int k = 0; k < d; ++k) rout[k] = a.dims[(int64_t)it.pair * 2 * d + (a.adjoint ? d + k : k)];
+            cx<float> *out = a.out + (int64_t)it.pair * a.out_tsize * a.nv + a.v0;
+            for (int j = pt; j < inner; j += NPAD) {
+                int rem = j;
+                bool pin = false;   // padded in some mode k >= 1
+                for (int k = d - 1; k >= 1; --k) {
+                    if (rem % a.out_R[k] >= rout[k]) pin = true;
+                    rem /= a.out_R[k];
+                }
+                for (int b0 = pin ? 0 : rout[0]; b0 < a.out_R[0]; ++b0) {
+                    cx<float> *o = out + ((int64_t)b0 * inner + j) * a.nv;
+                    int v = 0;
+                    if (vec)
+                        for (; v + 1 < a.nvc; v += 2) *reinterpret_cast<float4 *>(o + v) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    for (; v < a.nvc; ++v) o[v] = cx<float>{0.f, 0.f};
+                }
+            }
+        }
     }
 
-    if (!ok) {
-        if (tid == 0) atomicExch(a.err, (int)TB_ETIMEOUT);
-        // drain the copies this block issued and that may still be landing
-        for (int64_t gi = (g_copy > STAGES ? g_copy - STAGES : 0); gi < g_copy; ++gi)
-            mbar_wait(&full_bar[gi % STAGES], (uint32_t)((gi / STAGES) & 1));
-        if (g > 0) mbar_wait(&mma_bar[(g - 1) % STAGES], (uint32_t)(((g - 1) / STAGES) & 1));
-    }
     tc_fence_before();
     __syncthreads();
+    if (tid == 0 && abort_sh) {
+        // after a give-up, the copies of the last STAGES chunks may still be landing
+        for (int64_t gi = (issued > STAGES ? issued - STAGES : 0); gi < issued; ++gi)
+            mbar_wait(&full_bar[gi % STAGES], (uint32_t)((gi / STAGES) & 1));
+    }
     if (warp == 0) {
+        __syncwarp();
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
