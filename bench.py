@@ -277,7 +277,7 @@ def main():
     ms = max_over_ranks(ws, ms)
     value = ws * N * nv / (ms * 1e-3) / 1e9
     # kernel launches of one apply, counted from the per-pass event records
-    launches_per_step = int(round(sum(s["launches"] for s in stats) / max(args.steps, 1))) if stats else 0
+    launches_per_step = int(round(sum(s["kernels"] for s in stats) / max(args.steps, 1))) if stats else 0
 
     pk = peaks()
     dom = max(stats, key=lambda s: s["ms_total"]) if stats else None

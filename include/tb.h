@@ -207,17 +207,19 @@ typedef struct {
     char name[24];          /* "leaf_in", "split", "core", "gather", "leaf_out" */
     int level;              /* tree level of the pass (core: Lc) */
     int adjoint;            /* 1 for passes of tb_apply_adjoint */
-    int64_t launches;       /* kernel launches recorded */
-    double ms_total;        /* summed device time of those launches (CUDA events) */
-    int64_t bytes;          /* bytes one launch must move: its inputs, outputs and
-                               factors at their stored sizes */
-    double flops;           /* real floating-point operations of one launch */
+    int64_t launches;       /* executions of the pass recorded (one event pair each) */
+    double ms_total;        /* summed device time of those executions (CUDA events) */
+    int64_t bytes;          /* bytes one execution must move: its inputs, outputs
+                               and factors at their stored sizes */
+    double flops;           /* real floating-point operations of one execution */
+    int64_t kernels;        /* kernel launches inside the recorded executions */
 } tb_pass_stat;
 
 /*
  * Enable (on = 1) or disable per-pass timing: while enabled, every eager
- * apply records a CUDA event pair around each kernel launch on the apply's
- * stream.  Events add no work to the kernels themselves.
+ * apply records a CUDA event pair around each pass (the kernel launches of one
+ * step of Alg. 2) on the apply's stream.  Events add no work to the kernels
+ * themselves.
  */
 tb_status tb_profile_enable(tb_handle h, int on);
 

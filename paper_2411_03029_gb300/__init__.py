@@ -68,7 +68,7 @@ class _Info(ctypes.Structure):
 class _PassStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 24), ("level", ctypes.c_int), ("adjoint", ctypes.c_int),
                 ("launches", ctypes.c_int64), ("ms_total", ctypes.c_double), ("bytes", ctypes.c_int64),
-                ("flops", ctypes.c_double)]
+                ("flops", ctypes.c_double), ("kernels", ctypes.c_int64)]
 
 
 _LIB = None
@@ -200,7 +200,8 @@ class TBOperator:
         cnt = ctypes.c_int()
         _check(lib().tb_profile_stats(self._h, arr, 64, ctypes.byref(cnt)))
         return [{"name": a.name.decode(), "level": a.level, "adjoint": a.adjoint, "launches": a.launches,
-                 "ms_total": a.ms_total, "bytes": a.bytes, "flops": a.flops} for a in arr[: cnt.value]]
+                 "ms_total": a.ms_total, "bytes": a.bytes, "flops": a.flops, "kernels": a.kernels}
+                for a in arr[: cnt.value]]
 
     def _prep(self, x, precision):
         torch = _torch()

@@ -123,6 +123,8 @@ tb_status tb_free(tb_handle h) {
     for (void *p : h->allocations) cudaFree(p);
     if (h->ws.buf[0]) cudaFree(h->ws.buf[0]);
     if (h->ws.buf[1]) cudaFree(h->ws.buf[1]);
+    if (h->ws.mbuf[0]) cudaFree(h->ws.mbuf[0]);
+    if (h->ws.mbuf[1]) cudaFree(h->ws.mbuf[1]);
     if (h->ws.host_in) cudaFree(h->ws.host_in);
     if (h->ws.host_out) cudaFree(h->ws.host_out);
     cudaSetDevice(cur);
@@ -591,6 +593,32 @@ static tb_status build_sep_steps(tb_plan *h) {
     return TB_OK;
 }
 
+// Largest mode intermediates (entries per RHS) of all level passes, for the
+// even and the odd modes (the two ping-pong buffers).
+static void mode_sizes(const tb_plan *h, int64_t mm[2]) {
+    const int d = h->d;
+    mm[0] = mm[1] = 0;
+    auto chain = [&](const int *m, const int *o) {
+        for (int k = 0; k + 1 < d; ++k) {
+            int64_t sz = h->P;
+            for (int i = 0; i < d; ++i) sz *= i <= k ? o[i] : m[i];
+            mm[k & 1] = std::max(mm[k & 1], sz);
+        }
+    };
+    for (int side = 0; side < 2; ++side) {
+        const SideLevel *S = side == 0 ? h->src : h->tgt;
+        int m[TB_MAX_D], o[TB_MAX_D];
+        for (int k = 0; k < d; ++k) { m[k] = (int)h->cb[k]; o[k] = S[0].R[k]; }
+        chain(m, o);
+        chain(o, m);
+        for (int l = 1; l <= h->Lc; ++l) {
+            for (int k = 0; k < d; ++k) { m[k] = 2 * S[l - 1].R[k]; o[k] = S[l].R[k]; }
+            chain(m, o);
+            chain(o, m);
+        }
+    }
+}
+
 static tb_status build_impl(tb_plan *h, const tb_grids *grids) {
     const int d = h->d;
     TB_TRY(dalloc(h, &h->d_err, 1));
@@ -636,6 +664,7 @@ static tb_status build_impl(tb_plan *h, const tb_grids *grids) {
         lm = std::max(lm, h->P * prod_tile(h->tgt[l], d));
     }
     h->level_max = lm;
+    mode_sizes(h, h->mode_max);
     if (h->separable) {
         TB_TRY(build_sep_steps(h));
         int64_t N = 1;
@@ -768,7 +797,7 @@ extern "C" tb_status tb_query(tb_handle h, tb_info *info) {
     info->core_entries = h->core_entries;
     info->factor_entries = fe;
     info->level_entries_max = h->level_max;
-    info->device_bytes = h->device_bytes + (int64_t)h->ws.bytes * 2;
+    info->device_bytes = h->device_bytes + (int64_t)h->ws.bytes * 2 + (int64_t)(h->ws.mbytes[0] + h->ws.mbytes[1]);
     info->build_seconds = h->build_seconds;
     return TB_OK;
 }
@@ -833,6 +862,12 @@ tb_status pick_chunk(int d, const int *m, const int *o, int64_t nv, int64_t &nvc
     if (c > nv) c = nv;
     nvc = c;
     ChainSmem s = plan(nvc);
+    // buffers start on 32-byte boundaries (vector loads in the mode products)
+    auto up4 = [](int64_t v) { return (v + 3) & ~(int64_t)3; };
+    s.x = up4(s.x);
+    s.b0 = up4(s.b0);
+    s.b1 = up4(s.b1);
+    s.y = up4(s.y);
     offX = 0;
     offB0 = (int)s.x;
     offB1 = (int)(s.x + s.b0);
@@ -845,16 +880,22 @@ tb_status pick_chunk(int d, const int *m, const int *o, int64_t nv, int64_t &nvc
     return TB_OK;
 }
 
+// One level pass as d mode-product launches (tb_mode.cu).  T holds the two
+// ping-pong buffers of the mode intermediates.
 template <class R>
 tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out, int64_t nv,
-                     cudaStream_t st) {
+                     cudaStream_t st, void *const *T) {
     const int d = h->d, Lc = h->Lc;
-    LevelArgs<R> a;
+    const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
+    ModeArgs<R> a;
     std::memset(&a, 0, sizeof(a));
     a.d = d;
     a.Lc = Lc;
-    a.nF = ipow2(d * Lc);
+    a.pass = (int)pass;
     a.nv = nv;
+    a.nF = ipow2(d * Lc);
+    a.trans = (pass == Pass::LeafOut || pass == Pass::Gather) ? 1 : 0;
+    a.conj = conj ? 1 : 0;
     int m[TB_MAX_D], o[TB_MAX_D];
     const SideLevel *S = side == 0 ? h->src : h->tgt;
     for (int k = 0; k < d; ++k) {
@@ -870,36 +911,85 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
     switch (pass) {
         case Pass::LeafIn:
             a.user.p = (cx<R> *)in;
-            a.out = tilebuf<R>(h, side, 0, out);
+            a.lout = tilebuf<R>(h, side, 0, out);
             a.fac = facref<R>(h, side, 0);
             for (int k = 0; k < d; ++k) { m[k] = (int)h->cb[k]; o[k] = S[0].R[k]; }
-            a.nblocks = a.nF << (Lc * d);
             break;
         case Pass::LeafOut:
             a.user.p = (cx<R> *)out;
-            a.in = tilebuf<R>(h, side, 0, (void *)in);
+            a.lin = tilebuf<R>(h, side, 0, (void *)in);
             a.fac = facref<R>(h, side, 0);
             for (int k = 0; k < d; ++k) { m[k] = S[0].R[k]; o[k] = (int)h->cb[k]; }
-            a.nblocks = a.nF << (Lc * d);
             break;
         case Pass::Split:
-            a.in = tilebuf<R>(h, side, l - 1, (void *)in);
-            a.out = tilebuf<R>(h, side, l, out);
+            a.lin = tilebuf<R>(h, side, l - 1, (void *)in);
+            a.lout = tilebuf<R>(h, side, l, out);
             a.fac = facref<R>(h, side, l);
-            for (int k = 0; k < d; ++k) { m[k] = 2 * S[l - 1].R[k]; o[k] = S[l].R[k]; }
-            a.nblocks = h->P >> d;
+            for (int k = 0; k < d; ++k) { m[k] = 2 * S[l - 1].R[k]; o[k] = S[l].R[k]; a.Rp[k] = S[l - 1].R[k]; }
             break;
         case Pass::Gather:
-            a.in = tilebuf<R>(h, side, l, (void *)in);
-            a.out = tilebuf<R>(h, side, l - 1, out);
+            a.lin = tilebuf<R>(h, side, l, (void *)in);
+            a.lout = tilebuf<R>(h, side, l - 1, out);
             a.fac = facref<R>(h, side, l);
-            for (int k = 0; k < d; ++k) { m[k] = S[l].R[k]; o[k] = 2 * S[l - 1].R[k]; }
-            a.nblocks = h->P >> d;
+            for (int k = 0; k < d; ++k) { m[k] = S[l].R[k]; o[k] = 2 * S[l - 1].R[k]; a.Rp[k] = S[l - 1].R[k]; }
             break;
     }
-    TB_TRY(pick_chunk<R>(d, m, o, nv, a.nvc, a.smem, a.offX, a.offB0, a.offB1, a.offY, a.offA,
-                         pass == Pass::LeafIn, pass == Pass::LeafOut));
-    TB_CK(launch_level<R>(pass, conj, a, st));
+    a.lvl = leaf ? 0 : l;
+    a.lgs = Lc - a.lvl;
+    const size_t es = sizeof(cx<R>);
+    int64_t gtab = 0;
+    for (int k = 0; k < d; ++k) gtab += h->cb[k];
+    for (int k = 0; k < d; ++k) {
+        a.k = k;
+        a.m = m[k];
+        a.o = o[k];
+        int64_t pre = 1, post = nv, usz_in = nv, usz_out = nv;
+        for (int i = 0; i < k; ++i) pre *= o[i];
+        for (int i = k + 1; i < d; ++i) post *= m[i];
+        for (int i = 0; i < d; ++i) {
+            usz_in *= i < k ? o[i] : m[i];
+            usz_out *= i <= k ? o[i] : m[i];
+        }
+        a.pre = pre;
+        a.post = post;
+        a.cols = pre * post;
+        int ink = MK_UNIT, outk = MK_UNIT;
+        a.in_tile = 0;
+        a.out_tile = 0;
+        a.tin = nullptr;
+        a.tout = nullptr;
+        if (k == 0) {
+            if (pass == Pass::LeafIn) ink = MK_USER;
+            else if (pass == Pass::Split) ink = MK_PARENTS;
+            else a.in_tile = 1;
+        } else {
+            a.tin = (const cx<R> *)T[(k - 1) & 1];
+            a.in_usize = usz_in;
+        }
+        if (k == d - 1) {
+            if (pass == Pass::LeafOut) outk = MK_USER;
+            else if (pass == Pass::Gather) outk = MK_PARENTS;
+            else a.out_tile = 1;
+        } else {
+            a.tout = (cx<R> *)T[k & 1];
+            a.out_usize = usz_out;
+        }
+        const bool group = ink == MK_PARENTS || outk == MK_PARENTS;
+        a.nblk = (!leaf && group) ? (h->P >> d) : h->P;
+        a.ncb = (a.cols + 255) / 256;
+        const int nch = (o[k] + 15) / 16;
+        int ob = (o[k] + nch - 1) / nch;
+        ob += ob & 1;
+        a.lda = ob * nch;
+        a.fsz = m[k] * a.lda;
+        const int nfac = group ? (1 << d) : 1;
+        a.smem = (size_t)nfac * a.fsz * es +
+                 ((ink == MK_USER || outk == MK_USER) ? (size_t)gtab * sizeof(int) : 0);
+        if (a.smem > g_smem_optin)
+            return fail(TB_EUNSUPPORTED, "factor blocks of " + std::to_string(a.smem) +
+                                             " bytes exceed shared memory");
+        TB_CK(launch_mode<R>(ink, outk, ob, a, st));
+    }
     return TB_OK;
 }
 
@@ -1172,16 +1262,20 @@ template <class R>
 tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st, bool prof,
                     int precision, void *const *bufs = nullptr) {
     void *B[2] = {h->ws.buf[0], h->ws.buf[1]};
+    void *T[2] = {h->ws.mbuf[0], h->ws.mbuf[1]};
     if (bufs) {
         B[0] = bufs[0];
         B[1] = bufs[1];
+        T[0] = bufs[2];
+        T[1] = bufs[3];
     }
     if (h->separable) return run_sep<R>(h, adjoint, in, out, nv, st, prof, B);
     const int Lc = h->Lc, d = h->d;
     const int first = adjoint ? 1 : 0, second = 1 - first;   // side traversed first / last
     const size_t es = sizeof(cx<R>);
-    auto timed = [&](const char *name, int level, int64_t bytes, double flops, auto &&fn) -> tb_status {
-        ProfRec r{name, level, (int)adjoint, nullptr, nullptr, bytes, flops};
+    auto timed = [&](const char *name, int level, int64_t bytes, double flops, int kernels,
+                     auto &&fn) -> tb_status {
+        ProfRec r{name, level, (int)adjoint, nullptr, nullptr, bytes, flops, kernels};
         if (prof) {
             TB_CK(cudaEventCreate(&r.e0));
             TB_CK(cudaEventCreate(&r.e1));
@@ -1198,7 +1292,8 @@ tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t
         int64_t bytes = 0;
         double flops = 0;
         if (prof) pass_cost(h, p, side, l, nv, es, bytes, flops);
-        return timed(name, l, bytes, flops, [&] { return level_pass<R>(h, p, adjoint, side, l, i, o, nv, st); });
+        return timed(name, l, bytes, flops, d,
+                     [&] { return level_pass<R>(h, p, adjoint, side, l, i, o, nv, st, T); });
     };
     int cur = 0;
     TB_TRY(level(Pass::LeafIn, "leaf_in", first, 0, in, B[cur]));
@@ -1225,7 +1320,9 @@ tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t
                 flops = 8.0 * (double)h->core_entries * nv;
             }
         }
-        TB_TRY(timed("core", Lc, bytes, flops,
+        const int core_kernels =
+            (precision == TB_PREC_C64_SPLITBF16 && !h->separable) ? (int)((nv + 15) / 16) : 1;
+        TB_TRY(timed("core", Lc, bytes, flops, core_kernels,
                      [&] { return core_pass<R>(h, adjoint, B[cur], B[cur ^ 1], nv, st, precision); }));
         cur ^= 1;
     }
@@ -1239,18 +1336,27 @@ tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t
 
 tb_status ensure_workspace(tb_plan *h, int64_t nv) {
     const size_t need = (size_t)h->level_max * (size_t)nv * sizeof(c128);
-    if (need <= h->ws.bytes) return TB_OK;
+    const size_t mneed[2] = {(size_t)h->mode_max[0] * (size_t)nv * sizeof(c128),
+                             (size_t)h->mode_max[1] * (size_t)nv * sizeof(c128)};
+    if (need <= h->ws.bytes && mneed[0] <= h->ws.mbytes[0] && mneed[1] <= h->ws.mbytes[1]) return TB_OK;
     TB_CK(cudaDeviceSynchronize());
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
     for (int i = 0; i < 2; ++i) {
         if (h->ws.buf[i]) cudaFree(h->ws.buf[i]);
-        h->ws.buf[i] = nullptr;
+        if (h->ws.mbuf[i]) cudaFree(h->ws.mbuf[i]);
+        h->ws.buf[i] = h->ws.mbuf[i] = nullptr;
+        h->ws.mbytes[i] = 0;
     }
     h->ws.bytes = 0;
     for (int i = 0; i < 2; ++i) TB_CK(cudaMalloc(&h->ws.buf[i], need));
     for (int i = 0; i < 2; ++i) TB_CK(cudaMemset(h->ws.buf[i], 0, need));
     h->ws.bytes = need;
+    for (int i = 0; i < 2; ++i)
+        if (mneed[i] > 0) {
+            TB_CK(cudaMalloc(&h->ws.mbuf[i], mneed[i]));
+            h->ws.mbytes[i] = mneed[i];
+        }
     return TB_OK;
 }
 
@@ -1341,10 +1447,14 @@ extern "C" tb_status tb_apply_noalloc(tb_handle h, const void *f, void *u, int64
     const char *a0 = (const char *)f, *b0 = (const char *)u;
     if (a0 < b0 + (size_t)N * nv * es && b0 < a0 + (size_t)N * nv * es)
         return fail(TB_EINVAL, "input and output overlap");
-    // two level tensors (ping-pong) of the largest level, 256-byte aligned
-    const size_t half = ((size_t)h->level_max * (size_t)nv * es + 255) / 256 * 256;
-    if (2 * half > (size_t)TB_NOALLOC_SCRATCH_BYTES)
-        return fail(TB_EUNSUPPORTED, "tb_apply_noalloc needs " + std::to_string(2 * half) +
+    // two level tensors (ping-pong) of the largest level and the two mode
+    // intermediates, each 256-byte aligned
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t half = al((size_t)h->level_max * (size_t)nv * es);
+    const size_t mreg[2] = {al((size_t)h->mode_max[0] * (size_t)nv * es), al((size_t)h->mode_max[1] * (size_t)nv * es)};
+    const size_t total = 2 * half + mreg[0] + mreg[1];
+    if (total > (size_t)TB_NOALLOC_SCRATCH_BYTES)
+        return fail(TB_EUNSUPPORTED, "tb_apply_noalloc needs " + std::to_string(total) +
                                          " bytes of scratch; the fixed scratch holds " +
                                          std::to_string((size_t)TB_NOALLOC_SCRATCH_BYTES) + " (reduce nv)");
     if (h->device < 0 || h->device >= 64) return fail(TB_EINVAL, "device ordinal out of range");
@@ -1369,7 +1479,8 @@ extern "C" tb_status tb_apply_noalloc(tb_handle h, const void *f, void *u, int64
         cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
         g_smem_optin = (size_t)v;
     }
-    void *bufs[2] = {base, (unsigned char *)base + half};
+    unsigned char *sb = (unsigned char *)base;
+    void *bufs[4] = {sb, sb + half, sb + 2 * half, sb + 2 * half + mreg[0]};
     cudaStream_t st = (cudaStream_t)stream;
     if (precision == TB_PREC_C128) return run_chain<double>(h, false, f, u, nv, st, false, precision, bufs);
     return run_chain<float>(h, false, f, u, nv, st, false, precision, bufs);
@@ -1429,6 +1540,7 @@ extern "C" tb_status tb_profile_stats(tb_handle h, tb_pass_stat *stats, int cap,
             hit = &agg.back();
         }
         hit->launches += 1;
+        hit->kernels += r.kernels;
         hit->ms_total += ms;
         hit->bytes = r.bytes;
         hit->flops = r.flops;

@@ -1,31 +1,18 @@
-// Apply kernels of the tensor butterfly contraction (Alg. 2, Sec. 3.2).
+// Mid-level core contraction on CUDA cores (Alg. 2, step 2):
+//   G_{t,s} = K(t-bar, s-bar) x_{d+1..2d} F_{t,s}
+// for the complex128 / complex64 apply precisions (the split-BF16 tensor-core
+// form lives in tb_core_tc.cu), in two forms: a dense core per pair (t, s)
+// stored with compact ranks, and, for kernels that are a product over modes,
+// the Kronecker form K = kron_k K_k applied as a mode-product chain on a tile
+// staged in shared memory.  The adjoint uses K(t-bar, s-bar)^H.
 //
-// Every level pass works on tiles: a tile is the block F_{tau,s} (source side)
-// or G_{t,nu} (target side) restricted to one tuple of segments (one node per
-// mode), i.e. prod_k R_{l,k} entries with the nv right-hand sides innermost.
-// A thread block stages its tiles in shared memory and contracts them mode by
-// mode (the products prod_k x_k of Alg. 2) with the per-mode factor blocks
-// staged beside them:
-//
-//   LeafIn  : F_{t0,s} = F(s) prod_k x_k V-bar^{s,k}                 (Alg. 2, step 1, l = 0)
-//   Split   : F_{tau,s} = F_{p_tau,s} prod_k x_k diag_nu(W)          (Alg. 2, step 1, l > 0)
-//             one block reads the 2^d parent tiles once and writes all 2^d children
-//   core    : G_{t,s} = K(t-bar, s-bar) x_{d+1..2d} F_{t,s}          (Alg. 2, step 2)
-//   Gather  : G_{t,p_nu} += G_{t,nu} prod_k x_k diag_tau(P)           (Alg. 2, step 3, l > 0)
-//             one block sums the 2^d children in shared memory: no atomics,
-//             deterministic order
-//   LeafOut : G(t) = G_{t,s0} prod_k x_k U-bar^{t,k}                 (Alg. 2, step 3, l = 0)
-//
-// The adjoint K^H runs the same passes in reverse with conjugated factors:
-// a Split with conj(P), a Gather with conj(W)^T, LeafIn with conj(U), LeafOut
-// with conj(V)^T and the core with K(t-bar, s-bar)^H.
+// The level passes (Alg. 2, steps 1 and 3) run as per-mode launches in
+// tb_mode.cu.
 #include "tb_kernels.cuh"
 
 namespace tb {
 
-constexpr int AP_THREADS = 256;
 constexpr int CORE_THREADS = 256;
-constexpr int AB = 4;   // output rows per thread in the leaf passes
 
 // Staged factors are transposed: At[b * lda + a] = A[a][b] with lda = o rounded
 // up to a multiple of 4 and zero columns a >= o (see stage()).
@@ -72,7 +59,7 @@ TB_DEV void mode_pass_rows(const cx<R> *__restrict__ src, cx<R> *__restrict__ ds
 // Register-tiled form: each item computes 4 output rows x 2 adjacent columns
 // from the transposed factor At[b][a] (row stride lda, a multiple of 4, zero
 // padded), so one b step costs two vector loads of At, one vector load of the
-// column pair and 8 complex FMAs.  Needs post even.
+// column pair and 8 complex FMAs.  Needs post even and 16-byte aligned src / At.
 template <class R>
 TB_DEV void mode_pass_tile(const cx<R> *__restrict__ src, cx<R> *__restrict__ dst, const cx<R> *__restrict__ At,
                            int lda, int pre, int mk, int ok, int post, bool acc) {
@@ -87,14 +74,15 @@ TB_DEV void mode_pass_tile(const cx<R> *__restrict__ src, cx<R> *__restrict__ ds
 #pragma unroll
         for (int i = 0; i < 4; ++i) c[i][0] = c[i][1] = {R(0), R(0)};
         const cx<R> *s = src + (p * mk) * post + q;
-        const cx<R> *ap = At + a0;
-#pragma unroll 2
+        const cx<R> *arow = At + a0;
+#pragma unroll 4
         for (int b = 0; b < mk; ++b) {
-            const cx<R> x0 = s[b * post], x1 = s[b * post + 1];
-            const cx<R> *arow = ap + b * lda;
-            cx<R> av[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) av[i] = arow[i];
+            cx<R> x0, x1, av[4];
+            ld2(s, x0, x1);
+            ld2(arow, av[0], av[1]);
+            ld2(arow + 2, av[2], av[3]);
+            s += post;
+            arow += lda;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 cmac(c[i][0], av[i], x0);
@@ -157,73 +145,6 @@ TB_DEV void mode_chain(int d, const int *m, const int *o, cx<R> *const *As, cons
     mode_chain<R>(d, 0, d, m, o, As, X, b0, b1, Y, nvc, acc_last);
 }
 
-// First mode product of a source-leaf tile, read straight from the user tensor
-// (gathered through the per-mode grid-index tables gt[k][b]) into dst.
-template <class R>
-TB_DEV void leaf_first_pass(int d, const int *m, const int *o, const cx<R> *A, const int *const *gt,
-                            const int64_t *gstride, const cx<R> *__restrict__ user, int64_t nv, int64_t v0,
-                            cx<R> *dst, int nvc) {
-    int post = nvc;
-    for (int i = 1; i < d; ++i) post *= m[i];
-    const int mk = m[0], ok = o[0];
-    const int nab = (ok + AB - 1) / AB;
-    for (int it = threadIdx.x; it < nab * post; it += blockDim.x) {
-        const int q = it % post, ab = it / post, a0 = ab * AB;
-        int rq = q / nvc;
-        const int v = q - rq * nvc;
-        int64_t base = v0 + v;
-        for (int k = d - 1; k >= 1; --k) {
-            const int bk = rq % m[k];
-            rq /= m[k];
-            base += (int64_t)gt[k][bk] * gstride[k] * nv;
-        }
-        cx<R> c[AB];
-#pragma unroll
-        for (int i = 0; i < AB; ++i) c[i] = {R(0), R(0)};
-        int acol[AB];
-#pragma unroll
-        for (int i = 0; i < AB; ++i) acol[i] = min(a0 + i, ok - 1);
-        const int lda = lda_of(ok);
-        for (int b = 0; b < mk; ++b) {
-            const cx<R> x = user[base + (int64_t)gt[0][b] * gstride[0] * nv];
-#pragma unroll
-            for (int i = 0; i < AB; ++i) cmac(c[i], A[b * lda + acol[i]], x);
-        }
-#pragma unroll
-        for (int i = 0; i < AB; ++i)
-            if (a0 + i < ok) dst[(a0 + i) * post + q] = c[i];
-    }
-}
-
-// Last mode product of a target-leaf tile, written straight to the user tensor
-// (scattered through the grid-index tables).
-template <class R>
-TB_DEV void leaf_last_pass(int d, const int *m, const int *o, const cx<R> *A, const int *const *gt,
-                           const int64_t *gstride, cx<R> *__restrict__ user, int64_t nv, int64_t v0,
-                           const cx<R> *src, int nvc) {
-    const int k = d - 1;
-    int pre = 1;
-    for (int i = 0; i < k; ++i) pre *= o[i];
-    const int mk = m[k], ok = o[k], post = nvc;
-    for (int it = threadIdx.x; it < pre * ok * post; it += blockDim.x) {
-        const int v = it % post;
-        const int r = it / post;
-        const int a = r % ok, p = r / ok;
-        cx<R> c = {R(0), R(0)};
-        const cx<R> *s = src + p * mk * post + v;
-        const int lda = lda_of(ok);
-        for (int b = 0; b < mk; ++b) cmac(c, A[b * lda + a], s[b * post]);
-        int64_t addr = (int64_t)gt[k][a] * gstride[k];
-        int rp = p;
-        for (int i = k - 1; i >= 0; --i) {
-            const int ai = rp % o[i];
-            rp /= o[i];
-            addr += (int64_t)gt[i][ai] * gstride[i];
-        }
-        user[addr * nv + v0 + v] = c;
-    }
-}
-
 // Raise a kernel's dynamic shared-memory limit once to the device maximum, so
 // later launches (including those recorded into CUDA graphs) need no attribute
 // calls.
@@ -278,213 +199,6 @@ TB_DEV void stage(cx<R> *dst, const cx<R> *__restrict__ src, int r, int c, bool 
         }
         dst[e] = v;
     }
-}
-
-template <class R>
-TB_DEV int64_t tile_index(const TileBuf<R> &b, int64_t F, int64_t M, int64_t sflat, int64_t nF, int d) {
-    const int64_t blk = b.layout == 0 ? M * nF + F : F * b.nM + M;
-    return (blk << (b.lgseg * d)) + sflat;
-}
-
-template <class R>
-TB_DEV const cx<R> *fac_block(const FacRef<R> &f, int k, int64_t F, int64_t M, int sig, int d, int Lc) {
-    int64_t j;
-    if (!f.separable) j = ((F * f.nM + M) << f.lgseg) + sig;
-    else {
-        const int64_t Fk = (F >> (Lc * (d - 1 - k))) & ((1 << Lc) - 1);
-        const int64_t Mk = (M >> (f.l * (d - 1 - k))) & ((1 << f.l) - 1);
-        j = (((Fk << f.l) + Mk) << f.lgseg) + sig;
-    }
-    return f.A[k] + j * (int64_t)f.rows[k] * f.cols[k];
-}
-
-// ------------------------------------------------------------------ level pass
-template <class R, Pass PASS, bool CONJ>
-__global__ void __launch_bounds__(AP_THREADS, 2) k_level(const LevelArgs<R> a) {
-    extern __shared__ __align__(16) unsigned char smraw[];
-    cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
-    cx<R> *X = sm + a.offX, *B0 = sm + a.offB0, *B1 = sm + a.offB1, *Y = sm + a.offY, *Asm = sm + a.offA;
-    const int d = a.d, Lc = a.Lc;
-    // RHS chunks of one group are consecutive blocks, so the group's tiles are
-    // re-read from L2 rather than DRAM when nv is split into several chunks
-    const int64_t nch = (a.nv + a.nvc - 1) / a.nvc;
-    const int64_t g = blockIdx.x / nch;
-    const int64_t v0 = (int64_t)(blockIdx.x - g * nch) * a.nvc;
-    const int nvc = (int)((a.nv - v0) < a.nvc ? (a.nv - v0) : a.nvc);
-    const int tid = threadIdx.x;
-
-    // segment tuple, multiset and mid-level block of this thread block
-    const int lgs = (PASS == Pass::LeafIn || PASS == Pass::Split) ? a.out.lgseg : a.in.lgseg;
-    const int64_t nsd = (int64_t)1 << (lgs * d);
-    const int64_t sflat = g & (nsd - 1);
-    const int64_t rest = g >> (lgs * d);
-    int sig[MAXD];
-    for (int k = 0; k < d; ++k) sig[k] = (int)((sflat >> (lgs * (d - 1 - k))) & ((1 << lgs) - 1));
-
-    cx<R> *As[MAXD];
-    {
-        // staged factors: m x lda_of(o), with the factor block applied as is
-        // (LeafIn, Split) or transposed (LeafOut, Gather)
-        const bool tr = (PASS == Pass::LeafOut || PASS == Pass::Gather);
-        int off = 0;
-        for (int k = 0; k < d; ++k) {
-            As[k] = Asm + off;
-            const int ro = tr ? a.fac.cols[k] : a.fac.rows[k], rm = tr ? a.fac.rows[k] : a.fac.cols[k];
-            off += rm * lda_of(ro);
-        }
-    }
-
-    if (PASS == Pass::LeafIn || PASS == Pass::LeafOut) {
-        const int64_t F = rest;
-        // grid point of tile entry: axis k position F_k*nmid + sig_k*cb + b_k
-        int m[MAXD], o[MAXD];
-        for (int k = 0; k < d; ++k) {
-            if (PASS == Pass::LeafIn) { m[k] = a.cb[k]; o[k] = a.out.R[k]; }
-            else { m[k] = a.in.R[k]; o[k] = a.cb[k]; }
-        }
-        // grid index of leaf entry b along axis k
-        __shared__ int gtab[MAXD][64];
-        const int *gt[MAXD];
-        for (int k = 0; k < d; ++k) {
-            const int64_t Fk = (F >> (Lc * (d - 1 - k))) & ((1 << Lc) - 1);
-            for (int b = tid; b < a.cb[k]; b += blockDim.x)
-                gtab[k][b] = a.perm[k][Fk * a.nmid[k] + (int64_t)sig[k] * a.cb[k] + b];
-            gt[k] = gtab[k];
-            stage<R>(As[k], fac_block<R>(a.fac, k, F, 0, sig[k], d, Lc), a.fac.rows[k], a.fac.cols[k],
-                     PASS == Pass::LeafOut, CONJ);
-        }
-        __syncthreads();
-        if (PASS == Pass::LeafIn) {
-            // pass 0 gathers from the user tensor; the leaf tile is never staged
-            leaf_first_pass<R>(d, m, o, As[0], gt, a.user.gstride, a.user.p, a.nv, v0, d == 1 ? Y : B0, nvc);
-            __syncthreads();
-            mode_chain<R>(d, 1, d, m, o, As, B0, B0, B1, Y, nvc, false);
-            const int64_t t = tile_index<R>(a.out, F, 0, sflat, a.nF, d);
-            cx<R> *dst = a.out.p + t * a.out.tsize * a.nv + v0;
-            for (int e = tid; e < a.out.tsize * nvc; e += blockDim.x) {
-                const int v = e % nvc, b = e / nvc;
-                dst[(int64_t)b * a.nv + v] = Y[e];
-            }
-        } else {
-            const int64_t t = tile_index<R>(a.in, F, 0, sflat, a.nF, d);
-            const cx<R> *src = a.in.p + t * a.in.tsize * a.nv + v0;
-            for (int e = tid; e < a.in.tsize * nvc; e += blockDim.x) {
-                const int v = e % nvc, b = e / nvc;
-                X[e] = src[(int64_t)b * a.nv + v];
-            }
-            __syncthreads();
-            // passes 0 .. d-2 in shared memory, the last one scatters to the user tensor
-            const cx<R> *last = mode_chain<R>(d, 0, d - 1, m, o, As, X, B0, B1, Y, nvc, false);
-            leaf_last_pass<R>(d, m, o, As[d - 1], gt, a.user.gstride, a.user.p, a.nv, v0, last, nvc);
-        }
-        return;
-    }
-
-    // Split / Gather: a group of 2^d tiles (F, multiset children of pM, sig)
-    const int lvl = a.fac.l;                 // level of the factors (the finer multiset level)
-    const int64_t nMp = (int64_t)1 << (d * (lvl - 1));
-    const int64_t pM = rest % nMp, F = rest / nMp;
-    int pMk[MAXD];
-    for (int k = 0; k < d; ++k) pMk[k] = (int)((pM >> ((lvl - 1) * (d - 1 - k))) & ((1 << (lvl - 1)) - 1));
-    const int nchild = 1 << d;
-
-    if (PASS == Pass::Split) {
-        // combined parent tile: dims 2 R'_k, child c of the parent segments at c_k R'_k
-        int m[MAXD], o[MAXD];
-        for (int k = 0; k < d; ++k) { m[k] = 2 * a.in.R[k]; o[k] = a.out.R[k]; }
-        const int Tin = a.in.tsize;
-        for (int e = tid; e < nchild * Tin * nvc; e += blockDim.x) {
-            const int v = e % nvc;
-            const int r = e / nvc;
-            int b = r % Tin;
-            const int c = r / Tin;
-            int64_t sp = 0;
-            int comb = 0, stride = 1;
-            for (int k = d - 1; k >= 0; --k) {
-                const int bk = b % a.in.R[k];
-                b /= a.in.R[k];
-                const int ck = (c >> (d - 1 - k)) & 1;
-                comb += (ck * a.in.R[k] + bk) * stride;
-                stride *= m[k];
-            }
-            for (int k = 0; k < d; ++k) sp = (sp << (lgs + 1)) | (2 * sig[k] + ((c >> (d - 1 - k)) & 1));
-            const int64_t t = tile_index<R>(a.in, F, pM, sp, a.nF, d);
-            const int bb = r % Tin;
-            X[comb * nvc + v] = a.in.p[(t * Tin + bb) * a.nv + v0 + v];
-        }
-        for (int c = 0; c < nchild; ++c) {
-            int64_t M = 0;
-            for (int k = 0; k < d; ++k) M = (M << lvl) | (2 * pMk[k] + ((c >> (d - 1 - k)) & 1));
-            for (int k = 0; k < d; ++k)
-                stage<R>(As[k], fac_block<R>(a.fac, k, F, M, sig[k], d, Lc), a.fac.rows[k], a.fac.cols[k], false, CONJ);
-            __syncthreads();
-            mode_chain<R>(d, m, o, As, X, B0, B1, Y, nvc, false);
-            const int64_t t = tile_index<R>(a.out, F, M, sflat, a.nF, d);
-            cx<R> *dst = a.out.p + t * a.out.tsize * a.nv + v0;
-            for (int e = tid; e < a.out.tsize * nvc; e += blockDim.x) {
-                const int v = e % nvc, b = e / nvc;
-                dst[(int64_t)b * a.nv + v] = Y[e];
-            }
-            __syncthreads();
-        }
-    } else {   // Gather
-        int m[MAXD], o[MAXD];
-        for (int k = 0; k < d; ++k) { m[k] = a.in.R[k]; o[k] = 2 * a.out.R[k]; }
-        for (int c = 0; c < nchild; ++c) {
-            int64_t M = 0;
-            for (int k = 0; k < d; ++k) M = (M << lvl) | (2 * pMk[k] + ((c >> (d - 1 - k)) & 1));
-            const int64_t t = tile_index<R>(a.in, F, M, sflat, a.nF, d);
-            const cx<R> *src = a.in.p + t * a.in.tsize * a.nv + v0;
-            for (int e = tid; e < a.in.tsize * nvc; e += blockDim.x) {
-                const int v = e % nvc, b = e / nvc;
-                X[e] = src[(int64_t)b * a.nv + v];
-            }
-            for (int k = 0; k < d; ++k)
-                stage<R>(As[k], fac_block<R>(a.fac, k, F, M, sig[k], d, Lc), a.fac.rows[k], a.fac.cols[k], true, CONJ);
-            __syncthreads();
-            mode_chain<R>(d, m, o, As, X, B0, B1, Y, nvc, c > 0);
-        }
-        // scatter the combined output to the 2^d tiles (F, pM, 2 sig + e) one level up
-        const int Tout = a.out.tsize;
-        for (int e = tid; e < nchild * Tout * nvc; e += blockDim.x) {
-            const int v = e % nvc;
-            const int r = e / nvc;
-            int b = r % Tout;
-            const int c = r / Tout;
-            int comb = 0, stride = 1;
-            for (int k = d - 1; k >= 0; --k) {
-                const int bk = b % a.out.R[k];
-                b /= a.out.R[k];
-                const int ck = (c >> (d - 1 - k)) & 1;
-                comb += (ck * a.out.R[k] + bk) * stride;
-                stride *= o[k];
-            }
-            int64_t sp = 0;
-            for (int k = 0; k < d; ++k) sp = (sp << (lgs + 1)) | (2 * sig[k] + ((c >> (d - 1 - k)) & 1));
-            const int64_t t = tile_index<R>(a.out, F, pM, sp, a.nF, d);
-            a.out.p[(t * Tout + (r % Tout)) * a.nv + v0 + v] = Y[comb * nvc + v];
-        }
-    }
-}
-
-template <class R>
-cudaError_t launch_level(Pass pass, bool conj, const LevelArgs<R> &a, cudaStream_t st) {
-    const int64_t nchunks = (a.nv + a.nvc - 1) / a.nvc;
-    dim3 grid((unsigned)(a.nblocks * nchunks));
-    void (*fn)(const LevelArgs<R>) = nullptr;
-#define TB_PICK(P)                                                  \
-    fn = conj ? k_level<R, P, true> : k_level<R, P, false>;
-    switch (pass) {
-        case Pass::LeafIn: TB_PICK(Pass::LeafIn) break;
-        case Pass::Split: TB_PICK(Pass::Split) break;
-        case Pass::Gather: TB_PICK(Pass::Gather) break;
-        case Pass::LeafOut: TB_PICK(Pass::LeafOut) break;
-    }
-#undef TB_PICK
-    cudaError_t e = set_smem_once((const void *)fn, a.smem);
-    if (e != cudaSuccess) return e;
-    fn<<<grid, AP_THREADS, a.smem, st>>>(a);
-    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- dense core
@@ -651,8 +365,6 @@ cudaError_t launch_core_kron(bool adjoint, const CoreApplyArgs<R> &a, cudaStream
     return cudaGetLastError();
 }
 
-template cudaError_t launch_level<float>(Pass, bool, const LevelArgs<float> &, cudaStream_t);
-template cudaError_t launch_level<double>(Pass, bool, const LevelArgs<double> &, cudaStream_t);
 template cudaError_t launch_core_dense<float>(bool, const CoreApplyArgs<float> &, cudaStream_t);
 template cudaError_t launch_core_dense<double>(bool, const CoreApplyArgs<double> &, cudaStream_t);
 template cudaError_t launch_core_kron<float>(bool, const CoreApplyArgs<float> &, cudaStream_t);

@@ -47,6 +47,18 @@ template <class R> TB_HD void cmac_conj(cx<R> &acc, cx<R> a, cx<R> b) {
     acc.y = fma(-a.y, b.x, acc.y);
 }
 
+// Two consecutive complex values; one 16-byte vector load for complex64 (the
+// caller guarantees 16-byte alignment of p).
+TB_DEV void ld2(const cx<float> *p, cx<float> &a, cx<float> &b) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    a = cx<float>{v.x, v.y};
+    b = cx<float>{v.z, v.w};
+}
+TB_DEV void ld2(const cx<double> *p, cx<double> &a, cx<double> &b) {
+    a = p[0];
+    b = p[1];
+}
+
 // ---------------------------------------------------------------- kernels
 // Kernel descriptor as seen by device code.  For HELMHOLTZ, p[1] holds
 // kappa / (2 pi) so that the phase is formed in cycles.

@@ -84,28 +84,64 @@ struct FacRef {
     int separable;
 };
 
+// Tile index of (mid-level multiset F, multiset M, segment tuple sflat).
+template <class R>
+TB_DEV int64_t tile_index(const TileBuf<R> &b, int64_t F, int64_t M, int64_t sflat, int64_t nF, int d) {
+    const int64_t blk = b.layout == 0 ? M * nF + F : F * b.nM + M;
+    return (blk << (b.lgseg * d)) + sflat;
+}
+
+// Factor block of mode k for (F, M, segment sig) at the factor's level.
+template <class R>
+TB_DEV const cx<R> *fac_block(const FacRef<R> &f, int k, int64_t F, int64_t M, int sig, int d, int Lc) {
+    int64_t j;
+    if (!f.separable) j = ((F * f.nM + M) << f.lgseg) + sig;
+    else {
+        const int64_t Fk = (F >> (Lc * (d - 1 - k))) & ((1 << Lc) - 1);
+        const int64_t Mk = (M >> (f.l * (d - 1 - k))) & ((1 << f.l) - 1);
+        j = (((Fk << f.l) + Mk) << f.lgseg) + sig;
+    }
+    return f.A[k] + j * (int64_t)f.rows[k] * f.cols[k];
+}
+
 template <class R>
 struct UserArr {      // user tensor (n_1..n_d, nv) C order
     cx<R> *p;
     int64_t gstride[MAXD];   // element stride (in points) of axis k
 };
 
+// One mode product of a level pass applied to every unit (k_mode in tb_mode.cu).
+// A unit is a tile (leaf passes) or one child chain of a split / gather group;
+// its mode-k intermediate has dims (o_0..o_{k-1}, m_k..m_{d-1}) x nv with the
+// RHS innermost.  Columns of a unit: pre = prod_{i<k} o_i times post =
+// prod_{i>k} m_i * nv.
+enum ModeKind : int { MK_UNIT = 0, MK_PARENTS = 1, MK_USER = 2 };
+
 template <class R>
-struct LevelArgs {
-    int d, Lc;
-    int64_t nF;           // mid-level multisets per side, 2^(d Lc)
-    int64_t nv, nvc;      // RHS total and per-block chunk
-    int64_t nblocks;
+struct ModeArgs {
+    int d, k, Lc, pass;        // pass: 0 LeafIn, 1 Split, 2 Gather, 3 LeafOut
+    int m, o, lda, fsz;        // staged factor: m x lda (zero columns a >= o), fsz elements apart
+    int trans, conj;           // the factor block is applied as op(A) = A or A^T, conjugated or not
+    int64_t pre, post, cols;   // columns of one unit
+    int64_t nblk, ncb;         // units (or groups) of the launch, thread blocks per unit
+    int64_t nv, nF;
+    int lvl, lgs;              // factor level and segment bits per mode of the pass's tiles
+    int in_tile, out_tile;     // MK_UNIT input / output is the level tile instead of a unit buffer
     int cb[MAXD];
-    int64_t nmid[MAXD];   // n_k >> Lc
+    int64_t nmid[MAXD];
     const int *perm[MAXD];
-    TileBuf<R> in, out;
+    int Rp[MAXD];              // parent tile dims (split input, gather output)
     FacRef<R> fac;
+    TileBuf<R> lin, lout;      // level tensors read / written by the pass
     UserArr<R> user;
-    // smem layout (elements of cx<R>)
-    int offX, offB0, offB1, offY, offA;
+    const cx<R> *tin;          // unit buffers of the previous / this mode
+    cx<R> *tout;
+    int64_t in_usize, out_usize;
     size_t smem;
 };
+
+template <class R>
+cudaError_t launch_mode(int in_kind, int out_kind, int ob, const ModeArgs<R> &a, cudaStream_t st);
 
 template <class R>
 struct CoreApplyArgs {
@@ -214,8 +250,6 @@ cudaError_t launch_sep_fiber(const SepFiberArgs<R> &a, cudaStream_t st);
 
 enum class Pass { LeafIn, Split, Gather, LeafOut };
 
-template <class R>
-cudaError_t launch_level(Pass pass, bool conj, const LevelArgs<R> &a, cudaStream_t st);
 template <class R>
 cudaError_t launch_core_dense(bool adjoint, const CoreApplyArgs<R> &a, cudaStream_t st);
 template <class R>

@@ -31,6 +31,8 @@ struct SideLevel {
 struct Workspace {
     void *buf[2] = {nullptr, nullptr};
     size_t bytes = 0;          // per buffer
+    void *mbuf[2] = {nullptr, nullptr};   // mode intermediates of the level passes
+    size_t mbytes[2] = {0, 0};
     void *host_in = nullptr;   // device staging for tb_apply_host
     void *host_out = nullptr;
     size_t host_bytes = 0;
@@ -42,6 +44,7 @@ struct ProfRec {
     cudaEvent_t e0, e1;
     int64_t bytes;
     double flops;
+    int kernels = 1;   // kernel launches between the two events
 };
 
 struct GraphEntry {
@@ -103,6 +106,7 @@ struct tb_plan {
     int64_t sep_nidx[2][TB_MAX_D] = {{0}};   // row-pointer entries of a mode's steps
 
     int64_t level_max = 0;         // largest level tensor, entries per RHS
+    int64_t mode_max[2] = {0, 0};  // largest even / odd mode intermediate, entries per RHS
     tb::Workspace ws;
     std::vector<tb::GraphEntry> graphs;
     std::vector<void *> allocations;
