@@ -976,7 +976,10 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
         }
         const bool group = ink == MK_PARENTS || outk == MK_PARENTS;
         a.nblk = (!leaf && group) ? (h->P >> d) : h->P;
-        a.ncb = (a.cols + 255) / 256;
+        if (a.cols >= ((int64_t)1 << 31) || usz_in >= ((int64_t)1 << 31) || usz_out >= ((int64_t)1 << 31))
+            return fail(TB_EUNSUPPORTED, "a level tile with its RHS exceeds 2^31 entries (reduce nv)");
+        const int cpb = mode_cols_per_block();
+        a.ncb = (a.cols + cpb - 1) / cpb;
         const int nch = (o[k] + 15) / 16;
         int ob = (o[k] + nch - 1) / nch;
         ob += ob & 1;

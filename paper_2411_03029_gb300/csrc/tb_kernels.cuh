@@ -142,6 +142,7 @@ struct ModeArgs {
 
 template <class R>
 cudaError_t launch_mode(int in_kind, int out_kind, int ob, const ModeArgs<R> &a, cudaStream_t st);
+int mode_cols_per_block();
 
 template <class R>
 struct CoreApplyArgs {

@@ -26,41 +26,52 @@
 namespace tb {
 
 constexpr int MODE_THREADS = 256;
+#ifndef TB_MODE_NC
+#define TB_MODE_NC 1
+#endif
+constexpr int MODE_NC = TB_MODE_NC;        // output columns per thread
+constexpr int MODE_MAXCH = 1 << MAXD;      // children of a group
 
-// acc[i] += sum_{b < m} At[b][a0 + i] x(b), i < OB, At row stride lda.
-template <class R, int OB, class LD>
-TB_DEV void mode_rows(cx<R> (&acc)[OB], const cx<R> *__restrict__ At, int lda, int a0, int m, const LD &ld) {
+// acc[j][i] += sum_{b < m} At[b][a0 + i] x_j(b) for the NC columns j of a
+// thread, i < OB, At row stride lda.  Each factor load (a warp-wide broadcast)
+// feeds NC columns.
+template <class R, int OB, int NC, class LD>
+TB_DEV void mode_rows(cx<R> (&acc)[NC][OB], const cx<R> *__restrict__ At, int lda, int a0, int m, const LD &ld) {
     int b = 0;
-#pragma unroll 2
     for (; b + 4 <= m; b += 4) {
-        const cx<R> x0 = ld(b), x1 = ld(b + 1), x2 = ld(b + 2), x3 = ld(b + 3);
+        cx<R> x[NC][4];
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) x[j][t] = ld(j, b + t);
         const cx<R> *r = At + b * lda + a0;
 #pragma unroll
-        for (int i = 0; i < OB; i += 2) {
-            cx<R> u, w;
-            ld2(r + i, u, w);
-            cmac(acc[i], u, x0);
-            cmac(acc[i + 1], w, x0);
-            ld2(r + lda + i, u, w);
-            cmac(acc[i], u, x1);
-            cmac(acc[i + 1], w, x1);
-            ld2(r + 2 * lda + i, u, w);
-            cmac(acc[i], u, x2);
-            cmac(acc[i + 1], w, x2);
-            ld2(r + 3 * lda + i, u, w);
-            cmac(acc[i], u, x3);
-            cmac(acc[i + 1], w, x3);
-        }
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+            for (int i = 0; i < OB; i += 2) {
+                cx<R> u, w;
+                ld2(r + t * lda + i, u, w);
+#pragma unroll
+                for (int j = 0; j < NC; ++j) {
+                    cmac(acc[j][i], u, x[j][t]);
+                    cmac(acc[j][i + 1], w, x[j][t]);
+                }
+            }
     }
     for (; b < m; ++b) {
-        const cx<R> x = ld(b);
+        cx<R> x[NC];
+#pragma unroll
+        for (int j = 0; j < NC; ++j) x[j] = ld(j, b);
         const cx<R> *r = At + b * lda + a0;
 #pragma unroll
         for (int i = 0; i < OB; i += 2) {
             cx<R> u, w;
             ld2(r + i, u, w);
-            cmac(acc[i], u, x);
-            cmac(acc[i + 1], w, x);
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                cmac(acc[j][i], u, x[j]);
+                cmac(acc[j][i + 1], w, x[j]);
+            }
         }
     }
 }
@@ -86,209 +97,239 @@ __global__ void __launch_bounds__(MODE_THREADS) k_mode(const ModeArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<R> *As = reinterpret_cast<cx<R> *>(smraw);
     constexpr bool GROUP = (IN == MK_PARENTS || OUT == MK_PARENTS);
-    const int d = a.d, Lc = a.Lc, k = a.k;
+    constexpr bool USER = (IN == MK_USER || OUT == MK_USER);
+    constexpr int NC = MODE_NC;
+    // block-uniform pointers, set up by the first two warps
+    __shared__ const cx<R> *s_fac[MODE_MAXCH];
+    __shared__ const cx<R> *s_in[MODE_MAXCH];    // per child: input unit buffer / level tile
+    __shared__ cx<R> *s_out[MODE_MAXCH];         // per child: output unit buffer / level tile
+    __shared__ cx<R> *s_par[MODE_MAXCH];         // parent tiles by child-bit tuple (Split in, Gather out)
+    const int d = a.d, k = a.k, tid = threadIdx.x;
     const bool leaf = a.pass == 0 || a.pass == 3;
     const int nchild = GROUP ? (1 << d) : 1;
-    const int64_t blk = blockIdx.x / a.ncb;
-    const int64_t col = (blockIdx.x - blk * a.ncb) * (int64_t)blockDim.x + threadIdx.x;
-
-    // ---- the unit (or group) of this block
-    int64_t g = blk;
-    int c_unit = 0;
-    if (!leaf && !GROUP) {
-        g = blk >> d;
-        c_unit = (int)(blk & ((1 << d) - 1));
-    }
-    const int lgs = a.lgs;
-    const int64_t sflat = g & (((int64_t)1 << (lgs * d)) - 1);
-    const int64_t rest = g >> (lgs * d);
-    int sig[MAXD], pMk[MAXD];
-    for (int i = 0; i < d; ++i) sig[i] = (int)((sflat >> (lgs * (d - 1 - i))) & ((1 << lgs) - 1));
-    int64_t F = rest, pM = 0;
-    const int lvl = a.lvl;
-    if (!leaf) {
-        const int64_t nMp = (int64_t)1 << (d * (lvl - 1));
-        pM = rest % nMp;
-        F = rest / nMp;
-        for (int i = 0; i < d; ++i) pMk[i] = (int)((pM >> ((lvl - 1) * (d - 1 - i))) & ((1 << (lvl - 1)) - 1));
-    }
-    auto child_M = [&](int c) {
-        int64_t M = 0;
-        for (int i = 0; i < d; ++i) M = (M << lvl) | (2 * pMk[i] + ((c >> (d - 1 - i)) & 1));
-        return M;
-    };
-    auto unit_of = [&](int c) { return leaf ? g : (g << d) + c; };
-
-    // ---- stage the factor block(s) and, for leaf passes, the grid-index tables
-    for (int j = 0; j < nchild; ++j) {
-        const int c = GROUP ? j : c_unit;
-        const cx<R> *src = fac_block<R>(a.fac, k, F, leaf ? 0 : child_M(c), sig[k], d, Lc);
-        stage_fac<R>(As + (int64_t)j * a.fsz, src, a.fac.rows[k], a.fac.cols[k], a.trans != 0, a.conj != 0, a.lda);
-    }
+    const unsigned blk = blockIdx.x / (unsigned)a.ncb;
+    const unsigned cblk = blockIdx.x - blk * (unsigned)a.ncb;
     int *gt = reinterpret_cast<int *>(As + (int64_t)nchild * a.fsz);
     int goff[MAXD];
-    if (IN == MK_USER || OUT == MK_USER) {
+    {
         int off = 0;
         for (int i = 0; i < d; ++i) {
             goff[i] = off;
-            const int64_t Fi = (F >> (Lc * (d - 1 - i))) & ((1 << Lc) - 1);
-            for (int b = threadIdx.x; b < a.cb[i]; b += blockDim.x)
-                gt[off + b] = a.perm[i][Fi * a.nmid[i] + (int64_t)sig[i] * a.cb[i] + b];
             off += a.cb[i];
         }
     }
+
+    if (tid < 64) {
+        // ---- the unit (or group) of this block
+        const int Lc = a.Lc, lgs = a.lgs, lvl = a.lvl;
+        int64_t g = blk;
+        int c_unit = 0;
+        if (!leaf && !GROUP) {
+            g = blk >> d;
+            c_unit = (int)(blk & ((1u << d) - 1));
+        }
+        const int64_t sflat = g & (((int64_t)1 << (lgs * d)) - 1);
+        const int64_t rest = g >> (lgs * d);
+        int sig[MAXD], pMk[MAXD];
+        for (int i = 0; i < d; ++i) sig[i] = (int)((sflat >> (lgs * (d - 1 - i))) & ((1 << lgs) - 1));
+        int64_t F = rest, pM = 0;
+        if (!leaf) {
+            const int64_t nMp = (int64_t)1 << (d * (lvl - 1));
+            pM = rest & (nMp - 1);
+            F = rest >> (d * (lvl - 1));
+            for (int i = 0; i < d; ++i)
+                pMk[i] = (int)((pM >> ((lvl - 1) * (d - 1 - i))) & ((1 << (lvl - 1)) - 1));
+        }
+        const int j = tid;
+        if (j < nchild) {
+            const int c = GROUP ? j : c_unit;
+            int64_t M = 0;
+            if (!leaf)
+                for (int i = 0; i < d; ++i) M = (M << lvl) | (2 * pMk[i] + ((c >> (d - 1 - i)) & 1));
+            const int64_t unit = leaf ? g : (g << d) + c;
+            s_fac[j] = fac_block<R>(a.fac, k, F, M, sig[k], d, Lc);
+            if (a.in_tile)
+                s_in[j] = a.lin.p + tile_index<R>(a.lin, F, M, sflat, a.nF, d) * a.lin.tsize * a.nv;
+            else
+                s_in[j] = a.tin ? a.tin + unit * a.in_usize : nullptr;
+            if (a.out_tile)
+                s_out[j] = a.lout.p + tile_index<R>(a.lout, F, M, sflat, a.nF, d) * a.lout.tsize * a.nv;
+            else
+                s_out[j] = a.tout ? a.tout + unit * a.out_usize : nullptr;
+        }
+        if (GROUP && j < (1 << d)) {
+            // parent tile of child-bit tuple j: segments 2 sig_i + bit_i at level l-1
+            int64_t sp = 0;
+            for (int i = 0; i < d; ++i) sp = (sp << (lgs + 1)) | (2 * sig[i] + ((j >> (d - 1 - i)) & 1));
+            const TileBuf<R> &tb = IN == MK_PARENTS ? a.lin : a.lout;
+            s_par[j] = tb.p + tile_index<R>(tb, F, pM, sp, a.nF, d) * tb.tsize * a.nv;
+        }
+        if (USER) {
+            for (int i = 0; i < d; ++i) {
+                const int64_t Fi = (F >> (Lc * (d - 1 - i))) & ((1 << Lc) - 1);
+                for (int b = j; b < a.cb[i]; b += 64)
+                    gt[goff[i] + b] = a.perm[i][Fi * a.nmid[i] + (int64_t)sig[i] * a.cb[i] + b];
+            }
+        }
+    }
     __syncthreads();
-    if (col >= a.cols) return;
+    for (int j = 0; j < nchild; ++j)
+        stage_fac<R>(As + (int64_t)j * a.fsz, s_fac[j], a.fac.rows[k], a.fac.cols[k], a.trans != 0, a.conj != 0,
+                     a.lda);
+    __syncthreads();
 
     const int m = a.m, o = a.o, lda = a.lda;
-    const int64_t post = a.post, nv = a.nv;
-    const int64_t p = col / post, q = col - p * post;
-
-    // ---- input fiber of the column
-    auto in_base = [&](int c) -> const cx<R> * {
-        if (a.in_tile) {
-            const int64_t t = tile_index<R>(a.lin, F, leaf ? 0 : child_M(c), sflat, a.nF, d);
-            return a.lin.p + t * a.lin.tsize * nv;
-        }
-        return a.tin + unit_of(c) * a.in_usize;
-    };
-    const int64_t xoff = p * m * post + q;
-    const cx<R> *xb[2] = {nullptr, nullptr};
-    int64_t xs0 = 0;
-    int rp0 = 0;
-    const cx<R> *uin = nullptr;
-    int64_t gs0nv = 0;
-    if (IN == MK_PARENTS) {
-        // q = (i_1 .. i_{d-1}, v) over the combined dims 2 R'_i
-        int64_t rem = q / nv;
-        const int64_t v = q - rem * nv;
-        int cbits[MAXD];
-        int64_t erest = 0, stride = 1;
-        for (int i = d - 1; i >= 1; --i) {
-            const int ci2 = 2 * a.Rp[i];
-            const int ii = (int)(rem % ci2);
-            rem /= ci2;
-            cbits[i] = ii >= a.Rp[i];
-            erest += (ii - cbits[i] * a.Rp[i]) * stride;
-            stride *= a.Rp[i];
-        }
-        xs0 = stride * nv;
-        rp0 = a.Rp[0];
-        for (int c0 = 0; c0 < 2; ++c0) {
-            int64_t sp = 0;
-            for (int i = 0; i < d; ++i) sp = (sp << (lgs + 1)) | (2 * sig[i] + (i == 0 ? c0 : cbits[i]));
-            const int64_t t = tile_index<R>(a.lin, F, pM, sp, a.nF, d);
-            xb[c0] = a.lin.p + (t * a.lin.tsize + erest) * nv + v;
-        }
-    } else if (IN == MK_USER) {
-        int64_t rem = q / nv;
-        const int64_t v = q - rem * nv;
-        int64_t ub = 0;
-        for (int i = d - 1; i >= 1; --i) {
-            const int bi = (int)(rem % a.cb[i]);
-            rem /= a.cb[i];
-            ub += (int64_t)gt[goff[i] + bi] * a.user.gstride[i];
-        }
-        uin = a.user.p + ub * nv + v;
-        gs0nv = a.user.gstride[0] * nv;
-    }
-
-    // ---- output of the column
-    cx<R> *yb[2] = {nullptr, nullptr};
-    int rpl = 0;
-    cx<R> *uout = nullptr;
-    const int *gtl = gt;
-    int64_t gslnv = 0;
-    const int64_t yoff = p * o * post + q;
-    if (OUT == MK_PARENTS) {
-        // post = nv: p = (a_0 .. a_{d-2}) over the combined dims 2 R'_i, q = v
-        int64_t rem = p;
-        int cbits[MAXD];
-        int64_t erest = 0, stride = a.Rp[d - 1];
-        for (int i = d - 2; i >= 0; --i) {
-            const int ci2 = 2 * a.Rp[i];
-            const int ii = (int)(rem % ci2);
-            rem /= ci2;
-            cbits[i] = ii >= a.Rp[i];
-            erest += (ii - cbits[i] * a.Rp[i]) * stride;
-            stride *= a.Rp[i];
-        }
-        rpl = a.Rp[d - 1];
-        for (int cl = 0; cl < 2; ++cl) {
-            int64_t sp = 0;
-            for (int i = 0; i < d; ++i) sp = (sp << (lgs + 1)) | (2 * sig[i] + (i == d - 1 ? cl : cbits[i]));
-            const int64_t t = tile_index<R>(a.lout, F, pM, sp, a.nF, d);
-            yb[cl] = a.lout.p + (t * a.lout.tsize + erest) * nv + q;
-        }
-    } else if (OUT == MK_USER) {
-        int64_t rem = p, ub = 0;
-        for (int i = d - 2; i >= 0; --i) {
-            const int ai = (int)(rem % a.cb[i]);
-            rem /= a.cb[i];
-            ub += (int64_t)gt[goff[i] + ai] * a.user.gstride[i];
-        }
-        uout = a.user.p + ub * nv + q;
-        gtl = gt + goff[d - 1];
-        gslnv = a.user.gstride[d - 1] * nv;
-    }
-    auto out_base = [&](int c) -> cx<R> * {
-        if (a.out_tile) {
-            const int64_t t = tile_index<R>(a.lout, F, leaf ? 0 : child_M(c), sflat, a.nF, d);
-            return a.lout.p + t * a.lout.tsize * nv;
-        }
-        return a.tout + unit_of(c) * a.out_usize;
-    };
-    auto store = [&](const cx<R> (&acc)[OB], int a0, cx<R> *Y) {
+    const int post = (int)a.post, nv = (int)a.nv, cols = (int)a.cols;
+    const int col0 = (int)cblk * (MODE_THREADS * NC) + tid;
+    if (col0 >= cols) return;
+    bool valid[NC];
+    int pcol[NC], qcol[NC];
 #pragma unroll
-        for (int i = 0; i < OB; ++i) {
-            const int aa = a0 + i;
-            if (aa < o) {
-                if (OUT == MK_UNIT) Y[yoff + aa * post] = acc[i];
-                else if (OUT == MK_PARENTS) {
-                    const int hi = aa >= rpl;
-                    yb[hi][(int64_t)(aa - hi * rpl) * nv] = acc[i];
-                } else {
-                    uout[(int64_t)gtl[aa] * gslnv] = acc[i];
+    for (int j = 0; j < NC; ++j) {
+        int cc = col0 + j * MODE_THREADS;
+        valid[j] = cc < cols;
+        if (!valid[j]) cc = cols - 1;   // computes a duplicate, stores nothing
+        pcol[j] = cc / post;
+        qcol[j] = cc - pcol[j] * post;
+    }
+
+    // ---- per-column input
+    int xoff[NC];
+    const cx<R> *xp0[NC], *xp1[NC];
+    int xs0 = 0, rp0 = 0;
+    int64_t gs0nv = 0;
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        xoff[j] = pcol[j] * m * post + qcol[j];
+        xp0[j] = xp1[j] = nullptr;
+        if (IN == MK_PARENTS) {
+            // q = (i_1 .. i_{d-1}, v) over the combined dims 2 R'_i
+            int rem = qcol[j] / nv;
+            const int v = qcol[j] - rem * nv;
+            int bits = 0, erest = 0, stride = 1;
+            for (int i = d - 1; i >= 1; --i) {
+                const int ci2 = 2 * a.Rp[i];
+                const int ii = rem % ci2;
+                rem /= ci2;
+                const int bi = ii >= a.Rp[i];
+                bits |= bi << (d - 1 - i);
+                erest += (ii - bi * a.Rp[i]) * stride;
+                stride *= a.Rp[i];
+            }
+            xs0 = stride * nv;
+            rp0 = a.Rp[0];
+            xp0[j] = s_par[bits] + (int64_t)erest * nv + v;
+            xp1[j] = s_par[bits | (1 << (d - 1))] + (int64_t)erest * nv + v;
+        } else if (IN == MK_USER) {
+            int rem = qcol[j] / nv;
+            const int v = qcol[j] - rem * nv;
+            int64_t ub = 0;
+            for (int i = d - 1; i >= 1; --i) {
+                const int bi = rem % a.cb[i];
+                rem /= a.cb[i];
+                ub += (int64_t)gt[goff[i] + bi] * a.user.gstride[i];
+            }
+            xp0[j] = a.user.p + ub * nv + v;
+            gs0nv = a.user.gstride[0] * (int64_t)nv;
+        }
+    }
+
+    // ---- per-column output
+    int yoff[NC];
+    cx<R> *yp0[NC], *yp1[NC];
+    int rpl = 0;
+    int64_t gslnv = 0;
+    const int *gtl = gt + goff[d - 1];
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+        yoff[j] = pcol[j] * o * post + qcol[j];
+        yp0[j] = yp1[j] = nullptr;
+        if (OUT == MK_PARENTS) {
+            // post = nv: p = (a_0 .. a_{d-2}) over the combined dims 2 R'_i, q = v
+            int rem = pcol[j], bits = 0, erest = 0, stride = a.Rp[d - 1];
+            for (int i = d - 2; i >= 0; --i) {
+                const int ci2 = 2 * a.Rp[i];
+                const int ii = rem % ci2;
+                rem /= ci2;
+                const int bi = ii >= a.Rp[i];
+                bits |= bi << (d - 1 - i);
+                erest += (ii - bi * a.Rp[i]) * stride;
+                stride *= a.Rp[i];
+            }
+            rpl = a.Rp[d - 1];
+            yp0[j] = s_par[bits] + (int64_t)erest * nv + qcol[j];
+            yp1[j] = s_par[bits | 1] + (int64_t)erest * nv + qcol[j];
+        } else if (OUT == MK_USER) {
+            int rem = pcol[j];
+            int64_t ub = 0;
+            for (int i = d - 2; i >= 0; --i) {
+                const int ai = rem % a.cb[i];
+                rem /= a.cb[i];
+                ub += (int64_t)gt[goff[i] + ai] * a.user.gstride[i];
+            }
+            yp0[j] = a.user.p + ub * nv + qcol[j];
+            gslnv = a.user.gstride[d - 1] * (int64_t)nv;
+        }
+    }
+
+    auto store = [&](const cx<R> (&acc)[NC][OB], int a0, cx<R> *Y) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j) {
+            if (!valid[j]) continue;
+#pragma unroll
+            for (int i = 0; i < OB; ++i) {
+                const int aa = a0 + i;
+                if (aa < o) {
+                    if (OUT == MK_UNIT) Y[yoff[j] + aa * post] = acc[j][i];
+                    else if (OUT == MK_PARENTS) {
+                        if (aa < rpl) yp0[j][aa * nv] = acc[j][i];
+                        else yp1[j][(aa - rpl) * nv] = acc[j][i];
+                    } else {
+                        yp0[j][(int64_t)gtl[aa] * gslnv] = acc[j][i];
+                    }
                 }
             }
         }
     };
+    auto zero = [](cx<R> (&acc)[NC][OB]) {
+#pragma unroll
+        for (int j = 0; j < NC; ++j)
+#pragma unroll
+            for (int i = 0; i < OB; ++i) acc[j][i] = {R(0), R(0)};
+    };
 
     if (IN == MK_PARENTS) {
-        auto ld = [&](int b) {
-            const int hi = b >= rp0;
-            return xb[hi][(int64_t)(b - hi * rp0) * xs0];
+        auto ld = [&](int j, int b) {
+            const cx<R> *pp = b < rp0 ? xp0[j] + b * xs0 : xp1[j] + (b - rp0) * xs0;
+            return *pp;
         };
         for (int c = 0; c < nchild; ++c) {
-            cx<R> *Y = (OUT == MK_UNIT) ? out_base(c) : nullptr;
+            cx<R> *Y = s_out[c];
             for (int a0 = 0; a0 < lda; a0 += OB) {
-                cx<R> acc[OB];
-#pragma unroll
-                for (int i = 0; i < OB; ++i) acc[i] = {R(0), R(0)};
-                mode_rows<R, OB>(acc, As + (int64_t)c * a.fsz, lda, a0, m, ld);
+                cx<R> acc[NC][OB];
+                zero(acc);
+                mode_rows<R, OB, NC>(acc, As + (int64_t)c * a.fsz, lda, a0, m, ld);
                 store(acc, a0, Y);
             }
         }
     } else if (IN == MK_USER) {
-        auto ld = [&](int b) { return uin[(int64_t)gt[b] * gs0nv]; };
-        cx<R> *Y = (OUT == MK_UNIT) ? out_base(0) : nullptr;
+        auto ld = [&](int j, int b) { return xp0[j][(int64_t)gt[b] * gs0nv]; };
+        cx<R> *Y = s_out[0];
         for (int a0 = 0; a0 < lda; a0 += OB) {
-            cx<R> acc[OB];
-#pragma unroll
-            for (int i = 0; i < OB; ++i) acc[i] = {R(0), R(0)};
-            mode_rows<R, OB>(acc, As, lda, a0, m, ld);
+            cx<R> acc[NC][OB];
+            zero(acc);
+            mode_rows<R, OB, NC>(acc, As, lda, a0, m, ld);
             store(acc, a0, Y);
         }
     } else {
-        cx<R> *Y = (OUT == MK_UNIT) ? out_base(c_unit) : nullptr;
+        cx<R> *Y = s_out[0];
         for (int a0 = 0; a0 < lda; a0 += OB) {
-            cx<R> acc[OB];
-#pragma unroll
-            for (int i = 0; i < OB; ++i) acc[i] = {R(0), R(0)};
-            for (int j = 0; j < nchild; ++j) {   // children in a fixed order (Gather)
-                const cx<R> *X = in_base(GROUP ? j : c_unit) + xoff;
-                auto ld = [&](int b) { return X[(int64_t)b * post]; };
-                mode_rows<R, OB>(acc, As + (int64_t)j * a.fsz, lda, a0, m, ld);
+            cx<R> acc[NC][OB];
+            zero(acc);
+            for (int c = 0; c < nchild; ++c) {   // children in a fixed order (Gather)
+                const cx<R> *X = s_in[c];
+                auto ld = [&](int j, int b) { return X[xoff[j] + b * post]; };
+                mode_rows<R, OB, NC>(acc, As + (int64_t)c * a.fsz, lda, a0, m, ld);
             }
             store(acc, a0, Y);
         }
@@ -327,6 +368,8 @@ cudaError_t launch_mode(int in_kind, int out_kind, int ob, const ModeArgs<R> &a,
     if (in_kind == MK_UNIT && out_kind == MK_USER) return launch_mode_ob<R, MK_UNIT, MK_USER>(ob, a, st);
     return cudaErrorInvalidValue;
 }
+
+int mode_cols_per_block() { return MODE_THREADS * MODE_NC; }
 
 template cudaError_t launch_mode<float>(int, int, int, const ModeArgs<float> &, cudaStream_t);
 template cudaError_t launch_mode<double>(int, int, int, const ModeArgs<double> &, cudaStream_t);
