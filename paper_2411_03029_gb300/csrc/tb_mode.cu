@@ -32,21 +32,28 @@ constexpr int MODE_THREADS = 256;
 constexpr int MODE_NC = TB_MODE_NC;        // output columns per thread
 constexpr int MODE_MAXCH = 1 << MAXD;      // children of a group
 
+#ifndef TB_MODE_XB
+#define TB_MODE_XB 8
+#endif
+constexpr int MODE_XB = TB_MODE_XB;        // input values of a column loaded before use
+
 // acc[j][i] += sum_{b < m} At[b][a0 + i] x_j(b) for the NC columns j of a
-// thread, i < OB, At row stride lda.  Each factor load (a warp-wide broadcast)
-// feeds NC columns.
+// thread, i < OB, At row stride lda.  The column's inputs are loaded MODE_XB at
+// a time (all issued before the first use, so each thread keeps that many
+// loads in flight); each factor load (a warp-wide broadcast) feeds NC columns.
 template <class R, int OB, int NC, class LD>
 TB_DEV void mode_rows(cx<R> (&acc)[NC][OB], const cx<R> *__restrict__ At, int lda, int a0, int m, const LD &ld) {
-    int b = 0;
-    for (; b + 4 <= m; b += 4) {
-        cx<R> x[NC][4];
+    constexpr int XB = MODE_XB;
+    for (int b = 0; b < m; b += XB) {
+        cx<R> x[NC][XB];
 #pragma unroll
-        for (int j = 0; j < NC; ++j)
+        for (int t = 0; t < XB; ++t)
 #pragma unroll
-            for (int t = 0; t < 4; ++t) x[j][t] = ld(j, b + t);
+            for (int j = 0; j < NC; ++j) x[j][t] = (b + t < m) ? ld(j, b + t) : cx<R>{R(0), R(0)};
         const cx<R> *r = At + b * lda + a0;
 #pragma unroll
-        for (int t = 0; t < 4; ++t)
+        for (int t = 0; t < XB; ++t) {
+            if (b + t >= m) break;
 #pragma unroll
             for (int i = 0; i < OB; i += 2) {
                 cx<R> u, w;
@@ -56,21 +63,6 @@ TB_DEV void mode_rows(cx<R> (&acc)[NC][OB], const cx<R> *__restrict__ At, int ld
                     cmac(acc[j][i], u, x[j][t]);
                     cmac(acc[j][i + 1], w, x[j][t]);
                 }
-            }
-    }
-    for (; b < m; ++b) {
-        cx<R> x[NC];
-#pragma unroll
-        for (int j = 0; j < NC; ++j) x[j] = ld(j, b);
-        const cx<R> *r = At + b * lda + a0;
-#pragma unroll
-        for (int i = 0; i < OB; i += 2) {
-            cx<R> u, w;
-            ld2(r + i, u, w);
-#pragma unroll
-            for (int j = 0; j < NC; ++j) {
-                cmac(acc[j][i], u, x[j]);
-                cmac(acc[j][i + 1], w, x[j]);
             }
         }
     }
