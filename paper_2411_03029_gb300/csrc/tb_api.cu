@@ -44,6 +44,7 @@ static tb_status fail(tb_status s, const std::string &msg) {
 namespace {
 
 size_t g_smem_optin = 0;
+int64_t g_num_sms = 0;
 
 bool pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
 int ilog2(int64_t x) {
@@ -980,6 +981,9 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
             return fail(TB_EUNSUPPORTED, "a level tile with its RHS exceeds 2^31 entries (reduce nv)");
         const int cpb = mode_cols_per_block();
         a.ncb = (a.cols + cpb - 1) / cpb;
+        // enough blocks for a few waves of four resident blocks per SM
+        const int64_t target = 16 * (int64_t)g_num_sms;
+        a.gsplit = std::min<int64_t>(a.ncb, std::max<int64_t>(1, (target + a.nblk - 1) / a.nblk));
         const int nch = (o[k] + 15) / 16;
         int ob = (o[k] + nch - 1) / nch;
         ob += ob & 1;
@@ -1381,8 +1385,10 @@ tb_status apply_common(tb_handle h, const void *in, void *out, int64_t nv, int p
     if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(TB_EINVAL, "input and output overlap");
     if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
     if (g_smem_optin == 0) {
-        int v = 0;
+        int v = 0, sms = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        g_num_sms = sms;
         g_smem_optin = (size_t)v;
     }
     TB_TRY(ensure_workspace(h, nv));
@@ -1478,8 +1484,10 @@ extern "C" tb_status tb_apply_noalloc(tb_handle h, const void *f, void *u, int64
         base = g_noalloc_addr[h->device];
     }
     if (g_smem_optin == 0) {
-        int v = 0;
+        int v = 0, sms = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        g_num_sms = sms;
         g_smem_optin = (size_t)v;
     }
     unsigned char *sb = (unsigned char *)base;

@@ -123,7 +123,8 @@ struct ModeArgs {
     int m, o, lda, fsz;        // staged factor: m x lda (zero columns a >= o), fsz elements apart
     int trans, conj;           // the factor block is applied as op(A) = A or A^T, conjugated or not
     int64_t pre, post, cols;   // columns of one unit
-    int64_t nblk, ncb;         // units (or groups) of the launch, thread blocks per unit
+    int64_t nblk, ncb;         // units (or groups) of the launch, column chunks per unit
+    int64_t gsplit;            // thread blocks per unit; each walks every gsplit-th chunk
     int64_t nv, nF;
     int lvl, lgs;              // factor level and segment bits per mode of the pass's tiles
     int in_tile, out_tile;     // MK_UNIT input / output is the level tile instead of a unit buffer

@@ -99,8 +99,10 @@ __global__ void __launch_bounds__(MODE_THREADS) k_mode(const ModeArgs<R> a) {
     const int d = a.d, k = a.k, tid = threadIdx.x;
     const bool leaf = a.pass == 0 || a.pass == 3;
     const int nchild = GROUP ? (1 << d) : 1;
-    const unsigned blk = blockIdx.x / (unsigned)a.ncb;
-    const unsigned cblk = blockIdx.x - blk * (unsigned)a.ncb;
+    // block = (unit or group, first column chunk); it walks the unit's column
+    // chunks with stride gsplit, so the factor staging is paid once per block
+    const unsigned blk = blockIdx.x / (unsigned)a.gsplit;
+    const unsigned cfirst = blockIdx.x - blk * (unsigned)a.gsplit;
     int *gt = reinterpret_cast<int *>(As + (int64_t)nchild * a.fsz);
     int goff[MAXD];
     {
@@ -172,8 +174,9 @@ __global__ void __launch_bounds__(MODE_THREADS) k_mode(const ModeArgs<R> a) {
 
     const int m = a.m, o = a.o, lda = a.lda;
     const int post = (int)a.post, nv = (int)a.nv, cols = (int)a.cols;
+    for (unsigned cblk = cfirst; cblk < (unsigned)a.ncb; cblk += (unsigned)a.gsplit) {
     const int col0 = (int)cblk * (MODE_THREADS * NC) + tid;
-    if (col0 >= cols) return;
+    if (col0 >= cols) break;
     bool valid[NC];
     int pcol[NC], qcol[NC];
 #pragma unroll
@@ -326,6 +329,7 @@ __global__ void __launch_bounds__(MODE_THREADS) k_mode(const ModeArgs<R> a) {
             store(acc, a0, Y);
         }
     }
+    }   // column chunks
 }
 
 template <class R, int IN, int OUT>
@@ -344,7 +348,7 @@ cudaError_t launch_mode_ob(int ob, const ModeArgs<R> &a, cudaStream_t st) {
     }
     cudaError_t e = set_smem_once((const void *)fn, a.smem);
     if (e != cudaSuccess) return e;
-    const int64_t blocks = a.nblk * a.ncb;
+    const int64_t blocks = a.nblk * a.gsplit;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
     fn<<<(unsigned)blocks, MODE_THREADS, a.smem, st>>>(a);
