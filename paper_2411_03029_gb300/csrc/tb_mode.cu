@@ -36,6 +36,7 @@ constexpr int MODE_MAXCH = 1 << MAXD;      // children of a group
 #define TB_MODE_XB 8
 #endif
 constexpr int MODE_XB = TB_MODE_XB;        // input values of a column loaded before use
+constexpr int MODE_FIBER = 24;             // longest input fiber a Split's first mode keeps in registers
 
 // acc[j][i] += sum_{b < m} At[b][a0 + i] x_j(b) for the NC columns j of a
 // thread, i < OB, At row stride lda.  The column's inputs are loaded MODE_XB at
@@ -298,13 +299,41 @@ __global__ void __launch_bounds__(MODE_THREADS) k_mode(const ModeArgs<R> a) {
             const cx<R> *pp = b < rp0 ? xp0[j] + b * xs0 : xp1[j] + (b - rp0) * xs0;
             return *pp;
         };
-        for (int c = 0; c < nchild; ++c) {
-            cx<R> *Y = s_out[c];
-            for (int a0 = 0; a0 < lda; a0 += OB) {
-                cx<R> acc[NC][OB];
-                zero(acc);
-                mode_rows<R, OB, NC>(acc, As + (int64_t)c * a.fsz, lda, a0, m, ld);
-                store(acc, a0, Y);
+        if (NC == 1 && m <= MODE_FIBER) {
+            // the fiber is read once into registers and feeds all 2^d children
+            cx<R> xf[MODE_FIBER];
+#pragma unroll
+            for (int b = 0; b < MODE_FIBER; ++b) xf[b] = b < m ? ld(0, b) : cx<R>{R(0), R(0)};
+            for (int c = 0; c < nchild; ++c) {
+                cx<R> *Y = s_out[c];
+                const cx<R> *At = As + (int64_t)c * a.fsz;
+                for (int a0 = 0; a0 < lda; a0 += OB) {
+                    cx<R> acc[NC][OB];
+                    zero(acc);
+#pragma unroll
+                    for (int b = 0; b < MODE_FIBER; ++b) {
+                        if (b >= m) break;
+                        const cx<R> *r = At + b * lda + a0;
+#pragma unroll
+                        for (int i = 0; i < OB; i += 2) {
+                            cx<R> u, w;
+                            ld2(r + i, u, w);
+                            cmac(acc[0][i], u, xf[b]);
+                            cmac(acc[0][i + 1], w, xf[b]);
+                        }
+                    }
+                    store(acc, a0, Y);
+                }
+            }
+        } else {
+            for (int c = 0; c < nchild; ++c) {
+                cx<R> *Y = s_out[c];
+                for (int a0 = 0; a0 < lda; a0 += OB) {
+                    cx<R> acc[NC][OB];
+                    zero(acc);
+                    mode_rows<R, OB, NC>(acc, As + (int64_t)c * a.fsz, lda, a0, m, ld);
+                    store(acc, a0, Y);
+                }
             }
         }
     } else if (IN == MK_USER) {
