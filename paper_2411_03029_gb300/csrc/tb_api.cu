@@ -43,6 +43,9 @@ static tb_status fail(tb_status s, const std::string &msg) {
 
 namespace {
 
+#ifndef TB_MODE_WAVES
+#define TB_MODE_WAVES 32
+#endif
 size_t g_smem_optin = 0;
 int64_t g_num_sms = 0;
 
@@ -982,7 +985,7 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
         const int cpb = mode_cols_per_block();
         a.ncb = (a.cols + cpb - 1) / cpb;
         // enough blocks for a few waves of four resident blocks per SM
-        const int64_t target = 16 * (int64_t)g_num_sms;
+        const int64_t target = TB_MODE_WAVES * (int64_t)g_num_sms;
         a.gsplit = std::min<int64_t>(a.ncb, std::max<int64_t>(1, (target + a.nblk - 1) / a.nblk));
         const int nch = (o[k] + 15) / 16;
         int ob = (o[k] + nch - 1) / nch;

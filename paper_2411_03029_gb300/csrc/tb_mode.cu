@@ -25,7 +25,10 @@
 
 namespace tb {
 
-constexpr int MODE_THREADS = 256;
+#ifndef TB_MODE_THREADS
+#define TB_MODE_THREADS 128
+#endif
+constexpr int MODE_THREADS = TB_MODE_THREADS;
 #ifndef TB_MODE_NC
 #define TB_MODE_NC 1
 #endif
