@@ -47,6 +47,7 @@ def parse():
     p.add_argument("--precision", type=int, default=None, help="0 c128, 1 c64, 2 split-bf16")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
     p.add_argument("--err-samples", type=int, default=16)
     p.add_argument("--profile-only", action="store_true", help="eager applies only (for ncu)")
     p.add_argument("--n", type=int, default=None, help="points per axis of a reduced-size copy (profiling)")
@@ -268,6 +269,12 @@ def main():
     op = tb.from_workload(w, precisions=mask, use_graphs=not args.profile_only, precision=prec)
     info = op.info()
     nv = w.nv
+    tune_s = None
+    if not args.no_autotune:                # launch shapes for this nv and precision (tb_autotune)
+        t0 = time.perf_counter()
+        op.autotune(nv, prec)
+        torch.cuda.synchronize()
+        tune_s = time.perf_counter() - t0
     f_host = W.rhs(w)                       # complex128, CPU
     if ws > 1:                              # each replica applies its own batch
         f_host = W.complex_gaussian(f_host.shape, 10_000 + rank)
@@ -370,7 +377,8 @@ def main():
                       "L": info["L"], "ranks_src": info["rank_src"], "ranks_tgt": info["rank_tgt"],
                       "rank_min": info["rank_min"], "rank_max": info["rank_max"],
                       "core_entries": info["core_entries"], "build_s": info["build_seconds"],
-                      "l2": "inputs larger than L2 (no flush)", "graph": True},
+                      "l2": "inputs larger than L2 (no flush)", "graph": True,
+                      "autotune_s": tune_s},
            "roofline": roof, "passes": passes, "e2e": e2e,
            "gpu_launches": launches_per_step * args.steps}
 

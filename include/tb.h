@@ -92,6 +92,7 @@ typedef struct {
     int use_graphs;        /* 1 = replay each (f, u, nv, precision) apply as a CUDA graph */
     int device;            /* CUDA device ordinal; -1 = the current device */
     uint64_t seed;         /* seed of the proxy-row design (Sec. 2.1 proxy strategy) */
+    int autotune;          /* 1 = run tb_autotune before the first apply of each (nv, precision) */
 } tb_options;
 
 typedef struct tb_plan *tb_handle;
@@ -198,6 +199,23 @@ tb_status tb_apply_host(tb_handle h, const void *f, void *u, int64_t nv, int pre
 #define TB_NOALLOC_SCRATCH_BYTES (64ull << 20)
 tb_status tb_apply_noalloc(tb_handle h, const void *f, void *u, int64_t nv, int precision,
                            void *cuda_stream);
+
+/*
+ * Empirical tuning of the apply's launch shapes for nv right-hand sides at
+ * `precision`, on the handle's own factors and workspaces (the paper fixes no
+ * launch layout; this is the library's own schedule search):
+ *  - non-separable handles: for every level pass, side and mode, the output
+ *    rows per register tile (even values up to 16) and the number of thread
+ *    blocks per unit;
+ *  - separable handles: per-mode fiber passes against multi-mode tile passes.
+ * Each candidate runs a few times on `cuda_stream` (CUDA-event timed); the
+ * fastest is kept in the handle and used by every later apply (results are
+ * identical up to the summation order of separable passes).  Allocates two
+ * temporary N x nv device buffers and frees them before returning.  Not for
+ * use while the stream is being captured.  Status: TB_EINVAL on a bad handle,
+ * nv or precision, TB_ECUDA on a CUDA error.
+ */
+tb_status tb_autotune(tb_handle h, int64_t nv, int precision, void *cuda_stream);
 
 /* Describe a built handle (ranks, sizes, timings). */
 tb_status tb_query(tb_handle h, tb_info *info);

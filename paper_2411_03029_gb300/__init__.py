@@ -31,7 +31,7 @@ STATUS = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "TB_ERAN
 # every symbol declared in include/tb.h
 EXPORTS = ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
            "tb_apply_host", "tb_query", "tb_free", "tb_last_error", "tb_version",
-           "tb_profile_enable", "tb_profile_stats", "tb_apply_noalloc")
+           "tb_profile_enable", "tb_profile_stats", "tb_apply_noalloc", "tb_autotune")
 
 
 class TBError(RuntimeError):
@@ -51,7 +51,8 @@ class _Grids(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("order", ctypes.c_int), ("proxy_rows", ctypes.c_int),
                 ("rank_max", ctypes.c_int), ("precisions", ctypes.c_uint), ("separable", ctypes.c_int),
-                ("use_graphs", ctypes.c_int), ("device", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("use_graphs", ctypes.c_int), ("device", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("autotune", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -134,7 +135,7 @@ class TBOperator:
     def __init__(self, kind: int, d: int, n, xs, ys, tol: float, params=(), L: int = -1,
                  order: int = ORDER_AUTO, precisions: int = 0, separable: int = -1,
                  use_graphs: bool = False, proxy_rows: int = 1024, rank_max: int = 32,
-                 seed: int = 0x5eed, precision: int = PREC_C64):
+                 seed: int = 0x5eed, precision: int = PREC_C64, autotune: bool = False):
         L_ = lib()
         n = [int(v) for v in (n if np.iterable(n) else [n] * d)]
         self.d, self.n, self.kind = d, n, kind
@@ -150,6 +151,7 @@ class TBOperator:
         _check(L_.tb_options_default(ctypes.byref(opt)))
         opt.L, opt.order, opt.proxy_rows, opt.rank_max = L, order, proxy_rows, rank_max
         opt.precisions, opt.separable, opt.use_graphs, opt.seed = precisions, separable, int(use_graphs), seed
+        opt.autotune = int(autotune)
         try:
             opt.device = _torch().cuda.current_device()
         except Exception:  # pragma: no cover
@@ -189,6 +191,13 @@ class TBOperator:
             "level_entries_max": inf.level_entries_max, "device_bytes": inf.device_bytes,
             "build_seconds": inf.build_seconds,
         }
+
+    def autotune(self, nv: int = 1, precision: int | None = None):
+        """Tune the launch shapes for nv RHS at `precision` on the current stream (tb_autotune)."""
+        torch = _torch()
+        precision = self.precision if precision is None else precision
+        _check(lib().tb_autotune(self._h, int(nv), precision,
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
 
     def profile(self, on: bool = True):
         """Record CUDA events around every pass of eager applies (tb_profile_enable)."""

@@ -114,6 +114,7 @@ tb_status tb_options_default(tb_options *o) {
     o->use_graphs = 0;
     o->device = -1;
     o->seed = 0x5eed;
+    o->autotune = 0;
     return TB_OK;
 }
 
@@ -752,6 +753,7 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
         return fail(TB_EUNSUPPORTED, "requested apply precision is not built into this library");
     }
     h->use_graphs = opt.use_graphs;
+    h->autotune = opt.autotune;
     h->proxy_rows = opt.proxy_rows;
     h->rank_max = opt.rank_max;
     h->seed = opt.seed;
@@ -888,7 +890,7 @@ tb_status pick_chunk(int d, const int *m, const int *o, int64_t nv, int64_t &nvc
 // ping-pong buffers of the mode intermediates.
 template <class R>
 tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out, int64_t nv,
-                     cudaStream_t st, void *const *T) {
+                     cudaStream_t st, void *const *T, int only_k = -1, int ob_set = 0, int waves_set = 0) {
     const int d = h->d, Lc = h->Lc;
     const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
     ModeArgs<R> a;
@@ -943,7 +945,9 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
     const size_t es = sizeof(cx<R>);
     int64_t gtab = 0;
     for (int k = 0; k < d; ++k) gtab += h->cb[k];
+    const tb::ModeTune *tune = h->tune[std::is_same<R, double>::value ? 1 : 0][side][(int)pass][leaf ? 0 : l];
     for (int k = 0; k < d; ++k) {
+        if (only_k >= 0 && k != only_k) continue;
         a.k = k;
         a.m = m[k];
         a.o = o[k];
@@ -985,12 +989,16 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
         const int cpb = mode_cols_per_block();
         a.ncb = (a.cols + cpb - 1) / cpb;
         // enough blocks for a few waves of four resident blocks per SM
-        const int64_t target = TB_MODE_WAVES * (int64_t)g_num_sms;
+        const int waves = waves_set ? waves_set : (tune[k].waves > 0 ? tune[k].waves : TB_MODE_WAVES);
+        const int64_t target = waves * (int64_t)g_num_sms;
         a.gsplit = std::min<int64_t>(a.ncb, std::max<int64_t>(1, (target + a.nblk - 1) / a.nblk));
-        const int nch = (o[k] + 15) / 16;
-        int ob = (o[k] + nch - 1) / nch;
-        ob += ob & 1;
-        a.lda = ob * nch;
+        int ob = ob_set ? ob_set : tune[k].ob;
+        if (ob < 2 || ob > 16 || (ob & 1)) {   // built-in rule: fewest chunks of at most 16 rows
+            const int nch = (o[k] + 15) / 16;
+            ob = (o[k] + nch - 1) / nch;
+            ob += ob & 1;
+        }
+        a.lda = (o[k] + ob - 1) / ob * ob;
         a.fsz = m[k] * a.lda;
         const int nfac = group ? (1 << d) : 1;
         a.smem = (size_t)nfac * a.fsz * es +
@@ -1156,7 +1164,7 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
             smem[k] = (size_t)(2 * h->sep_maxext[k] * T * es + fixed + 16);
             fits = T >= 32;
         }
-        if (fits) {
+        if (fits && h->sep_choice != 2) {
             int i = 0;
             for (int k = d - 1; k >= 0; --k, ++i) {
                 SepFiberArgs<R> a;
@@ -1370,6 +1378,125 @@ tb_status ensure_workspace(tb_plan *h, int64_t nv) {
     return TB_OK;
 }
 
+// Output lengths o_k of the modes of a level pass (see level_pass).
+void pass_out_dims(const tb_plan *h, Pass pass, int side, int l, int *o) {
+    const SideLevel *S = side == 0 ? h->src : h->tgt;
+    for (int k = 0; k < h->d; ++k) {
+        switch (pass) {
+            case Pass::LeafIn: o[k] = S[0].R[k]; break;
+            case Pass::LeafOut: o[k] = (int)h->cb[k]; break;
+            case Pass::Split: o[k] = S[l].R[k]; break;
+            case Pass::Gather: o[k] = 2 * S[l - 1].R[k]; break;
+        }
+    }
+}
+
+// Empirical launch-shape search (tb_autotune): each candidate runs once to
+// warm up and three times under CUDA events on `st`; the fastest is kept.
+// `uin` / `uout` stand in for the user tensors (N x nv).
+template <class R>
+tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, const void *uin, void *uout) {
+    cudaEvent_t e0, e1;
+    TB_CK(cudaEventCreate(&e0));
+    TB_CK(cudaEventCreate(&e1));
+    tb_status status = TB_OK;
+    auto time_it = [&](auto &&fn, float &best) -> tb_status {
+        TB_TRY(fn());
+        best = 3.0e38f;
+        for (int r = 0; r < 3; ++r) {
+            TB_CK(cudaEventRecord(e0, st));
+            TB_TRY(fn());
+            TB_CK(cudaEventRecord(e1, st));
+            TB_CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            TB_CK(cudaEventElapsedTime(&ms, e0, e1));
+            best = std::min(best, ms);
+        }
+        return TB_OK;
+    };
+    if (h->separable) {
+        float best = 3.0e38f;
+        int choice = 0;
+        for (int c = 1; c <= 2 && status == TB_OK; ++c) {
+            h->sep_choice = c;
+            float t = 0.f;
+            status = time_it([&] { return run_chain<R>(h, false, uin, uout, nv, st, false, precision); }, t);
+            if (status == TB_OK && t < best) {
+                best = t;
+                choice = c;
+            }
+        }
+        h->sep_choice = choice;
+    } else {
+        void *B[2] = {h->ws.buf[0], h->ws.buf[1]};
+        void *T[2] = {h->ws.mbuf[0], h->ws.mbuf[1]};
+        const int ri = std::is_same<R, double>::value ? 1 : 0;
+        const Pass passes[4] = {Pass::LeafIn, Pass::Split, Pass::Gather, Pass::LeafOut};
+        const int waves[3] = {8, 32, 128};
+        for (int side = 0; side < 2 && status == TB_OK; ++side)
+            for (Pass p : passes) {
+                const bool leaf = p == Pass::LeafIn || p == Pass::LeafOut;
+                for (int l = leaf ? 0 : 1; l <= (leaf ? 0 : h->Lc) && status == TB_OK; ++l) {
+                    const void *in = p == Pass::LeafIn ? uin : B[0];
+                    void *out = p == Pass::LeafOut ? uout : (p == Pass::LeafIn ? B[0] : B[1]);
+                    int o[TB_MAX_D];
+                    pass_out_dims(h, p, side, l, o);
+                    for (int k = 0; k < h->d && status == TB_OK; ++k) {
+                        // rows per register tile: the even split of o_k into 1, 2 or 3 chunks
+                        int obs[3], nob = 0;
+                        for (int nch = 1; nch <= 3; ++nch) {
+                            int ob = (o[k] + nch - 1) / nch;
+                            ob += ob & 1;
+                            if (ob < 2 || ob > 16) continue;
+                            bool dup = false;
+                            for (int i = 0; i < nob; ++i) dup = dup || obs[i] == ob;
+                            if (!dup) obs[nob++] = ob;
+                        }
+                        tb::ModeTune best;
+                        float tbest = 3.0e38f;
+                        for (int i = 0; i < nob && status == TB_OK; ++i)
+                            for (int w : waves) {
+                                float t = 0.f;
+                                status = time_it(
+                                    [&] {
+                                        return level_pass<R>(h, p, false, side, l, in, out, nv, st, T, k, obs[i], w);
+                                    },
+                                    t);
+                                if (status != TB_OK) break;
+                                if (t < tbest) {
+                                    tbest = t;
+                                    best.ob = obs[i];
+                                    best.waves = w;
+                                }
+                            }
+                        h->tune[ri][side][(int)p][l][k] = best;
+                    }
+                }
+            }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (status == TB_OK) h->tuned.emplace_back(nv, precision);
+    return status;
+}
+
+tb_status init_device_attrs(const tb_plan *h) {
+    if (g_smem_optin == 0) {
+        int v = 0, sms = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        g_num_sms = sms;
+        g_smem_optin = (size_t)v;
+    }
+    return TB_OK;
+}
+
+bool is_tuned(const tb_plan *h, int64_t nv, int precision) {
+    for (auto &t : h->tuned)
+        if (t.first == nv && t.second == precision) return true;
+    return false;
+}
+
 tb_status apply_common(tb_handle h, const void *in, void *out, int64_t nv, int precision, void *stream,
                        bool adjoint) {
     if (!h) return fail(TB_EINVAL, "handle is NULL");
@@ -1396,6 +1523,16 @@ tb_status apply_common(tb_handle h, const void *in, void *out, int64_t nv, int p
     }
     TB_TRY(ensure_workspace(h, nv));
     cudaStream_t st = (cudaStream_t)stream;
+    if (h->autotune && !is_tuned(h, nv, precision)) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        TB_CK(cudaStreamIsCapturing(st, &cs));
+        if (cs == cudaStreamCaptureStatusNone) {
+            // the call's own tensors stand in for the user tensors; `out` is
+            // overwritten by the apply below
+            if (precision == TB_PREC_C128) TB_TRY(tune_impl<double>(h, nv, precision, st, in, out));
+            else TB_TRY(tune_impl<float>(h, nv, precision, st, in, out));
+        }
+    }
     auto launch_all = [&](bool prof) -> tb_status {
         if (precision == TB_PREC_C128) return run_chain<double>(h, adjoint, in, out, nv, st, prof, precision);
         return run_chain<float>(h, adjoint, in, out, nv, st, prof, precision);
@@ -1432,6 +1569,38 @@ extern "C" tb_status tb_apply(tb_handle h, const void *f, void *u, int64_t nv, i
 
 extern "C" tb_status tb_apply_adjoint(tb_handle h, const void *g, void *v, int64_t nv, int precision, void *stream) {
     return apply_common(h, g, v, nv, precision, stream, true);
+}
+
+extern "C" tb_status tb_autotune(tb_handle h, int64_t nv, int precision, void *stream) {
+    if (!h) return fail(TB_EINVAL, "handle is NULL");
+    if (nv <= 0) return fail(TB_EINVAL, "nv must be positive");
+    if (precision < TB_PREC_C128 || precision > TB_PREC_C64_SPLITBF16)
+        return fail(TB_EINVAL, "unknown precision");
+    if (!(h->precisions & (1u << precision)))
+        return fail(TB_EUNSUPPORTED, "handle was built without precision " + std::to_string(precision));
+    if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
+    TB_TRY(init_device_attrs(h));
+    TB_TRY(ensure_workspace(h, nv));
+    int64_t N = 1;
+    for (int k = 0; k < h->d; ++k) N *= h->n[k];
+    const size_t bytes = (size_t)N * nv * (precision == TB_PREC_C128 ? 16 : 8);
+    void *uin = nullptr, *uout = nullptr;
+    TB_CK(cudaMalloc(&uin, bytes));
+    if (cudaMalloc(&uout, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(uin);
+        return fail(TB_ENOMEM, "tb_autotune: temporary buffers");
+    }
+    tb_status s = cudaMemsetAsync(uin, 0, bytes, (cudaStream_t)stream) == cudaSuccess ? TB_OK
+                                                                                     : fail(TB_ECUDA, "memset");
+    if (s == TB_OK) {
+        s = precision == TB_PREC_C128 ? tune_impl<double>(h, nv, precision, (cudaStream_t)stream, uin, uout)
+                                      : tune_impl<float>(h, nv, precision, (cudaStream_t)stream, uin, uout);
+    }
+    cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(uin);
+    cudaFree(uout);
+    return s;
 }
 
 // ------------------------------------------------- apply without allocating

@@ -47,6 +47,13 @@ struct ProfRec {
     int kernels = 1;   // kernel launches between the two events
 };
 
+// Launch shape of one mode-product launch picked by tb_autotune (0 = the
+// built-in rule).
+struct ModeTune {
+    int ob = 0;      // output rows per register tile
+    int waves = 0;   // thread blocks per SM the grid is sized for
+};
+
 struct GraphEntry {
     const void *in;
     void *out;
@@ -105,6 +112,11 @@ struct tb_plan {
     int64_t sep_nnz[2][TB_MAX_D] = {{0}};
     int64_t sep_nidx[2][TB_MAX_D] = {{0}};   // row-pointer entries of a mode's steps
 
+    // launch shapes chosen by tb_autotune: [complex64 / complex128][side][pass][level][mode]
+    tb::ModeTune tune[2][2][4][TB_MAX_LEVELS][TB_MAX_D];
+    int sep_choice = 0;            // separable apply: 0 rule, 1 per-mode fiber passes, 2 multi-mode tile passes
+    int autotune = 0;              // tune at the first apply of each (nv, precision)
+    std::vector<std::pair<int64_t, int>> tuned;   // (nv, precision) pairs tuned so far
     int64_t level_max = 0;         // largest level tensor, entries per RHS
     int64_t mode_max[2] = {0, 0};  // largest even / odd mode intermediate, entries per RHS
     tb::Workspace ws;
