@@ -580,14 +580,45 @@ static tb_status build_sep_steps(tb_plan *h) {
         TB_CK(cudaMemcpy(d_col, cols.data(), cols.size() * sizeof(int), cudaMemcpyHostToDevice));
         TB_CK(cudaMemcpy(d_v64, v64.data(), v64.size() * sizeof(c128), cudaMemcpyHostToDevice));
         TB_CK(cudaMemcpy(d_v32, v32.data(), v32.size() * sizeof(c64), cudaMemcpyHostToDevice));
+        // packed row-ordered streams (one zero entry for an empty row)
+        std::vector<SepNz<double>> p64;
+        std::vector<SepNz<float>> p32;
+        std::vector<std::pair<int64_t, int>> poff;   // (offset, count) per step
+        for (auto &s : all[dir]) {
+            const int64_t o0 = (int64_t)p64.size();
+            for (int r = 0; r < s.n_out; ++r) {
+                const int j0 = s.rowptr[(size_t)r], j1 = s.rowptr[(size_t)r + 1];
+                if (j0 == j1) {
+                    p64.push_back(SepNz<double>{c128{0.0, 0.0}, 0, 1});
+                    p32.push_back(SepNz<float>{c64{0.f, 0.f}, 0, 1});
+                }
+                for (int j = j0; j < j1; ++j) {
+                    const auto v = s.val[(size_t)j];
+                    p64.push_back(SepNz<double>{c128{v.real(), v.imag()}, s.col[(size_t)j], j + 1 == j1 ? 1 : 0});
+                    p32.push_back(SepNz<float>{c64{(float)v.real(), (float)v.imag()}, s.col[(size_t)j],
+                                               j + 1 == j1 ? 1 : 0});
+                }
+            }
+            poff.push_back({o0, (int)((int64_t)p64.size() - o0)});
+        }
+        SepNz<double> *d_p64 = nullptr;
+        SepNz<float> *d_p32 = nullptr;
+        TB_TRY(dalloc(h, &d_p64, (int64_t)std::max<size_t>(p64.size(), 1)));
+        TB_TRY(dalloc(h, &d_p32, (int64_t)std::max<size_t>(p32.size(), 1)));
+        TB_CK(cudaMemcpy(d_p64, p64.data(), p64.size() * sizeof(p64[0]), cudaMemcpyHostToDevice));
+        TB_CK(cudaMemcpy(d_p32, p32.data(), p32.size() * sizeof(p32[0]), cudaMemcpyHostToDevice));
+        for (int k = 0; k < d; ++k) {
+            h->sep_npk[dir][k] = 0;
+            for (int i = 0; i < h->sep_nsteps[dir][k]; ++i) h->sep_npk[dir][k] += poff[(size_t)(h->sep_step0[dir][k] + i)].second;
+        }
         std::vector<SepStep<double>> s64;
         std::vector<SepStep<float>> s32;
         for (size_t i = 0; i < all[dir].size(); ++i) {
             const HostStep &s = all[dir][i];
             s64.push_back(SepStep<double>{s.n_out, s.n_in, d_idx + off[i].first, d_col + off[i].second,
-                                          d_v64 + off[i].second});
+                                          d_v64 + off[i].second, d_p64 + poff[i].first, poff[i].second});
             s32.push_back(SepStep<float>{s.n_out, s.n_in, d_idx + off[i].first, d_col + off[i].second,
-                                         d_v32 + off[i].second});
+                                         d_v32 + off[i].second, d_p32 + poff[i].first, poff[i].second});
         }
         TB_TRY(dalloc(h, &h->sep64[dir], (int64_t)s64.size()));
         TB_TRY(dalloc(h, &h->sep32[dir], (int64_t)s32.size()));
@@ -1157,7 +1188,7 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
         size_t smem[TB_MAX_D];
         bool fits = true;
         for (int k = 0; k < d && fits; ++k) {
-            const int64_t fixed = h->sep_nnz[dir][k] * (es + 4) + h->sep_nidx[dir][k] * 4;
+            const int64_t fixed = h->sep_npk[dir][k] * (int64_t)sizeof(SepNz<R>);
             int T = 256;
             while (T >= 32 && 2 * h->sep_maxext[k] * T * es + fixed > limit) T /= 2;
             threads[k] = T;
@@ -1180,8 +1211,7 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
                 a.steps = sepptr<R>(h, dir) + h->sep_step0[dir][k];
                 a.nsteps = h->sep_nsteps[dir][k];
                 a.maxext = h->sep_maxext[k];
-                a.nnz = (int)h->sep_nnz[dir][k];
-                a.nidx = (int)h->sep_nidx[dir][k];
+                a.npk = (int)h->sep_npk[dir][k];
                 a.threads = threads[k];
                 a.smem = smem[k];
                 ProfRec r{"sep_mode", k, (int)adjoint, nullptr, nullptr, 0, 0.0};

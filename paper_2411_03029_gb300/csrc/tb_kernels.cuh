@@ -204,12 +204,24 @@ int core_tc_cols_per_chunk();
 // mode's chain (leaf V, transfers W, core K_k, transfers P, leaf U) is stored
 // as a list of sparse step matrices (CSR, explicit zeros dropped) acting on
 // the 1-D index of that mode.
+// One nonzero of a step in row order, for the fiber kernel: its value, its
+// column and whether it closes its row (rows without nonzeros carry one zero
+// entry, so every row closes exactly once).
+template <class R>
+struct alignas(16) SepNz {
+    cx<R> v;
+    int col;
+    int last;
+};
+
 template <class R>
 struct SepStep {
     int n_out, n_in;
     const int *rowptr;   // n_out + 1
     const int *col;
     const cx<R> *val;
+    const SepNz<R> *nz;  // the same step as a packed row-ordered stream
+    int npk;             // entries of nz
 };
 
 template <class R>
@@ -242,7 +254,7 @@ struct SepFiberArgs {
     cx<R> *out;
     const SepStep<R> *steps;  // this mode's steps, in order
     int nsteps, maxext;
-    int nnz, nidx;            // total nonzeros / row-pointer entries of the steps
+    int npk;                  // packed entries of all the steps
     int threads;
     size_t smem;
 };

@@ -111,6 +111,7 @@ struct tb_plan {
     int sep_maxext[TB_MAX_D] = {0};   // largest 1-D index along a mode's chain
     int64_t sep_nnz[2][TB_MAX_D] = {{0}};
     int64_t sep_nidx[2][TB_MAX_D] = {{0}};   // row-pointer entries of a mode's steps
+    int64_t sep_npk[2][TB_MAX_D] = {{0}};    // packed nonzero-stream entries of a mode's steps
 
     // launch shapes chosen by tb_autotune: [complex64 / complex128][side][pass][level][mode]
     tb::ModeTune tune[2][2][4][TB_MAX_LEVELS][TB_MAX_D];

@@ -84,34 +84,32 @@ template cudaError_t launch_sep_pass<double>(const SepPassArgs<double> &, cudaSt
 // Thread-per-fiber form: each thread owns one (fiber along mode k, RHS) pair
 // and keeps the fiber in its own column of two shared buffers (column-major
 // per thread: entry e of thread t at e * T + t, conflict-free), so the steps
-// of the chain need no block-wide synchronisation.  The steps' nonzeros sit in
-// shared memory and are read as broadcasts.
+// of the chain need no block-wide synchronisation.  Each step runs as its
+// packed row-ordered nonzero stream (value, column, end of row), copied to
+// shared memory with the column pre-scaled by T and read as broadcasts: one
+// 16-byte load, one operand load and four FMAs per nonzero.
 template <class R>
 __global__ void k_sep_fiber(const SepFiberArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int T = blockDim.x, t = threadIdx.x;
     cx<R> *b0 = reinterpret_cast<cx<R> *>(smraw);
     cx<R> *b1 = b0 + (size_t)a.maxext * T;
-    cx<R> *sval = b1 + (size_t)a.maxext * T;
-    int *sidx = reinterpret_cast<int *>(sval + a.nnz);   // row pointers, then columns
-    __shared__ int s_rp[40], s_cv[40];                    // per-step offsets
+    SepNz<R> *spk = reinterpret_cast<SepNz<R> *>(b1 + (size_t)a.maxext * T);
+    __shared__ int s_po[40];   // per-step offsets into spk
     if (t == 0) {
-        int rp = 0, cv = 0;
+        int po = 0;
         for (int s = 0; s < a.nsteps; ++s) {
-            s_rp[s] = rp;
-            s_cv[s] = cv;
-            rp += a.steps[s].n_out + 1;
-            cv += a.steps[s].rowptr[a.steps[s].n_out];
+            s_po[s] = po;
+            po += a.steps[s].npk;
         }
     }
     __syncthreads();
     for (int s = 0; s < a.nsteps; ++s) {
         const SepStep<R> S = a.steps[s];
-        const int nz = S.rowptr[S.n_out];
-        for (int i = t; i <= S.n_out; i += T) sidx[s_rp[s] + i] = S.rowptr[i];
-        for (int i = t; i < nz; i += T) {
-            sidx[a.nidx + s_cv[s] + i] = S.col[i];
-            sval[s_cv[s] + i] = S.val[i];
+        for (int i = t; i < S.npk; i += T) {
+            SepNz<R> e = S.nz[i];
+            e.col *= T;
+            spk[s_po[s] + i] = e;
         }
     }
     __syncthreads();
@@ -121,23 +119,28 @@ __global__ void k_sep_fiber(const SepFiberArgs<R> a) {
     const int64_t base = o * a.nk * a.inner + q;
     if (live)
         for (int i = 0; i < a.nk; ++i) b0[i * T + t] = a.in[base + (int64_t)i * a.inner];
-    cx<R> *src = b0, *dst = b1;
+    cx<R> *src = b0 + t, *dst = b1 + t;
     for (int s = 0; s < a.nsteps; ++s) {
-        const int nout = a.steps[s].n_out;
-        const int *rp = sidx + s_rp[s];
-        const int *cl = sidx + a.nidx + s_cv[s];
-        const cx<R> *vl = sval + s_cv[s];
-        for (int r = 0; r < nout; ++r) {
-            cx<R> acc = {R(0), R(0)};
-            for (int j = rp[r]; j < rp[r + 1]; ++j) cmac(acc, vl[j], src[cl[j] * T + t]);
-            dst[r * T + t] = acc;
+        const SepNz<R> *P = spk + s_po[s];
+        const int n = a.steps[s].npk;
+        cx<R> acc = {R(0), R(0)};
+        cx<R> *dp = dst;
+#pragma unroll 4
+        for (int j = 0; j < n; ++j) {
+            const SepNz<R> e = P[j];
+            cmac(acc, e.v, src[e.col]);
+            if (e.last) {
+                *dp = acc;
+                dp += T;
+                acc = {R(0), R(0)};
+            }
         }
         cx<R> *tmp = src;
         src = dst;
         dst = tmp;
     }
     if (live)
-        for (int i = 0; i < a.nk; ++i) a.out[base + (int64_t)i * a.inner] = src[i * T + t];
+        for (int i = 0; i < a.nk; ++i) a.out[base + (int64_t)i * a.inner] = src[i * T];
 }
 
 template <class R>
