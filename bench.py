@@ -150,7 +150,7 @@ class ClockSampler:
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload,
 # precision and pass; see profiles/ for the command.  Entries are removed when
 # the kernel changes.
-TRAFFIC = {("helmholtz3d_n256", 2, "core@l2"): 6.07e9 + 645.46e6}
+TRAFFIC = {}
 
 
 def level_mode_bytes(info, w, nv, es):

@@ -325,22 +325,54 @@ static tb_status build_cores(tb_plan *h) {
         const int NTc = core_tc_rows_per_item(), KCc = core_tc_cols_per_chunk();
         for (int dir = 0; dir < 2; ++dir) {
             std::vector<CoreItem> items;
+            std::vector<int> xpos;   // per pair: padded position of each compact input index (-1 = none)
+            const SideLevel &Sin = dir ? h->tgt[h->Lc] : h->src[h->Lc];
             int64_t boff = 0;
             for (int64_t p = 0; p < h->P; ++p) {
                 int64_t mt = 1, ms = 1;
+                int rin[TB_MAX_D], rout[TB_MAX_D];
                 for (int k = 0; k < d; ++k) {
-                    mt *= dims[(size_t)p * 2 * d + k];
-                    ms *= dims[(size_t)p * 2 * d + d + k];
+                    const int rt = dims[(size_t)p * 2 * d + k], rs = dims[(size_t)p * 2 * d + d + k];
+                    mt *= rt;
+                    ms *= rs;
+                    rin[k] = dir ? rt : rs;
+                    rout[k] = dir ? rs : rt;
                 }
                 const int64_t nrows = dir ? ms : mt, ncols = dir ? mt : ms;
                 const int64_t np = (nrows + 15) / 16 * 16;
                 const int nkc = (int)((ncols + KCc - 1) / KCc);
+                const int64_t x0 = (int64_t)xpos.size();
+                for (int64_t c = 0; c < (int64_t)nkc * KCc; ++c) {
+                    int pos = -1;
+                    if (c < ncols) {
+                        int64_t idx = c;
+                        int stride = 1;
+                        pos = 0;
+                        for (int k = d - 1; k >= 0; --k) {
+                            pos += (int)(idx % rin[k]) * stride;
+                            idx /= rin[k];
+                            stride *= Sin.R[k];
+                        }
+                    }
+                    xpos.push_back(pos);
+                }
                 for (int64_t j = 0; j * NTc < np; ++j) {
                     const int rows = (int)std::min<int64_t>(NTc, np - j * NTc);
-                    items.push_back(CoreItem{(int)p, (int)j, rows, nkc, boff});
+                    CoreItem it;
+                    std::memset(&it, 0, sizeof(it));
+                    it.pair = (int)p;
+                    it.tile = (int)j;
+                    it.rows = rows;
+                    it.nkc = nkc;
+                    it.boff = boff;
+                    it.xpos = x0;
+                    for (int k = 0; k < d; ++k) it.rout[k] = rout[k];
+                    items.push_back(it);
                     boff += (int64_t)nkc * rows * 256;
                 }
             }
+            TB_TRY(dalloc(h, &h->tc_xpos[dir], (int64_t)std::max<size_t>(xpos.size(), 1)));
+            TB_CK(cudaMemcpy(h->tc_xpos[dir], xpos.data(), xpos.size() * sizeof(int), cudaMemcpyHostToDevice));
             h->tc_nitems[dir] = (int64_t)items.size();
             h->tc_bytes[dir] = boff;
             TB_TRY(dalloc(h, &h->tc_items[dir], (int64_t)items.size()));
@@ -1061,6 +1093,7 @@ tb_status core_pass_tc(const tb_plan *h, bool adjoint, const void *in, void *out
     a.adjoint = dir;
     a.nitems = h->tc_nitems[dir];
     a.items = h->tc_items[dir];
+    a.xpos = h->tc_xpos[dir];
     a.tiles = h->tc_tiles[dir];
     a.dims = h->core_dims;
     a.in = tin.p;

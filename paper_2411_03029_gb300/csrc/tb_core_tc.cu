@@ -26,8 +26,9 @@
 // with warp-specialised roles that meet at mbarriers:
 //   warp 0       streams the core K-chunks into STAGES shared-memory stages
 //                (cp.async.bulk, completion counted in bytes);
-//   warps 8..11  load the matching 32 x 16 input values (three chunks ahead),
-//                split them into BF16 pairs and write the B rows of the stage;
+//   warps 8..11  load the matching 32 x 16 input values (three chunks ahead,
+//                through a build-time table of padded input positions), split
+//                them into BF16 pairs and write the B rows of the stage;
 //   warp 1       issues the MMAs of a chunk once both halves of its stage have
 //                landed and releases the stage with tcgen05.commit;
 //   warps 4..7   drain a finished item's accumulator from tensor memory and
@@ -328,52 +329,44 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
     } else if (warp >= CONV_WARP0) {
         // ------------------------------------------- input split into BF16 rows
         const int t = tid - CONV_WARP0 * 32;
-        const int kl = t >> 2, vq = (t & 3) * 4;   // column kl of the chunk, RHS vq .. vq+3
-        // look-ahead cursor: the next chunk whose input values are loaded, with
-        // the metadata of its item (read once per item)
+        const int kq = t >> 4, v = t & 15;   // columns 4 kq .. 4 kq + 3 of a chunk, RHS v
+        const bool vlive = v < a.nvc;
+        // Look-ahead cursor over (item, chunk).  The padded positions of the
+        // cursor's four columns (a build-time table, -1 past the pair's last
+        // column) are loaded one call before the values that use them, and the
+        // item after the cursor's is fetched one item early, so no value load
+        // waits on a table or item load issued in the same call.
         int64_t litem = blockIdx.x;
-        int lkc = 0, lnkc = 0, lM = 0;
-        int lr[MAXD];
-        const cx<float> *lbase = a.in;
-        auto meta = [&]() {
-            if (litem >= a.nitems) return;
-            const CoreItem it = a.items[litem];
-            lnkc = it.nkc;
-            lM = 1;
-            for (int k = 0; k < d; ++k) {
-                lr[k] = a.dims[(int64_t)it.pair * 2 * d + (a.adjoint ? k : d + k)];
-                lM *= lr[k];
-            }
-            lbase = a.in + (int64_t)it.pair * a.in_tsize * a.nv + a.v0 + vq;
+        int lkc = 0;
+        CoreItem lit, lnext;
+        if (litem < a.nitems) lit = a.items[litem];
+        if (litem + gridDim.x < a.nitems) lnext = a.items[litem + gridDim.x];
+        int4 lps = make_int4(-1, -1, -1, -1);
+        auto load_pos = [&]() {
+            if (litem < a.nitems) lps = *reinterpret_cast<const int4 *>(a.xpos + lit.xpos + lkc * KC + 4 * kq);
         };
-        const bool vec = (a.nv & 1) == 0 && vq + 4 <= a.nvc;   // two aligned 16-byte loads
+        load_pos();
         auto load_next = [&](cx<float> *x) {
 #pragma unroll
             for (int i = 0; i < 4; ++i) x[i] = cx<float>{0.f, 0.f};
             if (litem >= a.nitems) return;
-            const int k = lkc * KC + kl;
-            if (k < lM) {
-                const cx<float> *src = lbase + (int64_t)compact_to_padded(k, d, lr, a.in_R) * a.nv;
-                if (vec) {
-                    const float4 u = *reinterpret_cast<const float4 *>(src);
-                    const float4 w = *reinterpret_cast<const float4 *>(src + 2);
-                    x[0] = cx<float>{u.x, u.y};
-                    x[1] = cx<float>{u.z, u.w};
-                    x[2] = cx<float>{w.x, w.y};
-                    x[3] = cx<float>{w.z, w.w};
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        if (vq + i < a.nvc) x[i] = src[i];
-                }
+            const cx<float> *base = a.in + (int64_t)lit.pair * a.in_tsize * a.nv + a.v0 + v;
+            if (vlive) {
+                if (lps.x >= 0) x[0] = base[(int64_t)lps.x * a.nv];
+                if (lps.y >= 0) x[1] = base[(int64_t)lps.y * a.nv];
+                if (lps.z >= 0) x[2] = base[(int64_t)lps.z * a.nv];
+                if (lps.w >= 0) x[3] = base[(int64_t)lps.w * a.nv];
             }
-            if (++lkc >= lnkc) {
+            if (++lkc >= lit.nkc) {
                 lkc = 0;
                 litem += gridDim.x;
-                meta();
+                if (litem < a.nitems) {
+                    lit = lnext;
+                    if (litem + gridDim.x < a.nitems) lnext = a.items[litem + gridDim.x];
+                }
             }
+            load_pos();   // for the next call
         };
-        meta();
         // three chunks of values in flight, in fixed registers (no copies of
         // values that may still be loading)
         cx<float> b0[4], b1[4], b2[4];
@@ -391,19 +384,22 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
                 return false;
             }
             unsigned char *X = sm + s * STAGE_BYTES + CORE_BYTES;
-            const uint32_t bo = 4u * kl;
+            // rows v, 16 + v, 32 + v, 48 + v; bytes 16 kq .. 16 kq + 15 (columns 4 kq .. 4 kq + 3)
+            uint32_t w[4][4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int v = vq + i;
                 const float xr = x[i].x, xi = x[i].y;
                 const float hr = __bfloat162float(__float2bfloat16_rn(xr));
                 const float hi = __bfloat162float(__float2bfloat16_rn(xi));
                 const float lr_ = xr - hr, li = xi - hi;
-                *reinterpret_cast<uint32_t *>(X + swz(v, bo)) = pack_bf16(hr, -hi);
-                *reinterpret_cast<uint32_t *>(X + swz(16 + v, bo)) = pack_bf16(hi, hr);
-                *reinterpret_cast<uint32_t *>(X + swz(32 + v, bo)) = pack_bf16(lr_, -li);
-                *reinterpret_cast<uint32_t *>(X + swz(48 + v, bo)) = pack_bf16(li, lr_);
+                w[0][i] = pack_bf16(hr, -hi);
+                w[1][i] = pack_bf16(hi, hr);
+                w[2][i] = pack_bf16(lr_, -li);
+                w[3][i] = pack_bf16(li, lr_);
             }
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+                *reinterpret_cast<uint4 *>(X + swz(16 * f + v, 16u * kq)) = make_uint4(w[f][0], w[f][1], w[f][2], w[f][3]);
             fence_proxy_async();   // generic-proxy writes -> visible to the MMA
             mbar_arrive(&xfull_bar[s]);
             ++gi;
@@ -447,15 +443,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
             mbar_arrive(&acce_bar[b]);
 
             const int p = it.pair;
-            int rout[MAXD], Mout = 1;
-            for (int k = 0; k < d; ++k) {
-                rout[k] = a.dims[(int64_t)p * 2 * d + (a.adjoint ? d + k : k)];
-                Mout *= rout[k];
-            }
+            int Mout = 1;
+            for (int k = 0; k < d; ++k) Mout *= it.rout[k];
             cx<float> *out = a.out + (int64_t)p * a.out_tsize * a.nv;
             const int nl = 32 * q + lane, n = it.tile * NT + nl;
             if (nl < it.rows && n < Mout) {
-                const int pos = compact_to_padded(n, d, rout, a.out_R);
+                const int pos = compact_to_padded(n, d, it.rout, a.out_R);
                 cx<float> *o = out + (int64_t)pos * a.nv + a.v0;
                 if ((a.nv & 1) == 0 && (a.v0 & 1) == 0) {   // 16-byte aligned pairs
 #pragma unroll
@@ -486,8 +479,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
         for (int64_t item = blockIdx.x; item < a.nitems && !*abort; item += gridDim.x) {
             const CoreItem it = a.items[item];
             if (it.tile != 0) continue;
-            int rout[MAXD];
-            for (int k = 0; k < d; ++k) rout[k] = a.dims[(int64_t)it.pair * 2 * d + (a.adjoint ? d + k : k)];
+            const int *rout = it.rout;
             cx<float> *out = a.out + (int64_t)it.pair * a.out_tsize * a.nv + a.v0;
             for (int j = pt; j < inner; j += NPAD) {
                 int rem = j;

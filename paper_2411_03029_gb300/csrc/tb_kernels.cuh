@@ -165,7 +165,9 @@ struct CoreApplyArgs {
 // are stored as consecutive blocks of rows x 256 bytes (hi then lo BF16).
 struct CoreItem {
     int pair, tile, rows, nkc;
-    int64_t boff;   // byte offset of the item's first block
+    int64_t boff;      // byte offset of the item's first block
+    int64_t xpos;      // offset of the pair's input-position table (nkc x 32 entries)
+    int rout[MAXD];    // compact ranks of the pair on the output side (rows of this operator)
 };
 
 struct CoreTileArgs {
@@ -185,6 +187,7 @@ struct CoreTcArgs {
     const CoreItem *items;
     const unsigned char *tiles;
     const int *dims;
+    const int *xpos;   // per pair: padded tile position of each compact input index, -1 past the end
     const cx<float> *in;
     cx<float> *out;
     int in_tsize, out_tsize;

@@ -92,6 +92,7 @@ struct tb_plan {
     // K(t-bar, s-bar), [1] adjoint K(t-bar, s-bar)^H (see tb_core_tc.cu)
     unsigned char *tc_tiles[2] = {nullptr, nullptr};
     tb::CoreItem *tc_items[2] = {nullptr, nullptr};
+    int *tc_xpos[2] = {nullptr, nullptr};   // input-position tables of the tensor-core contraction
     int64_t tc_nitems[2] = {0, 0};
     int64_t tc_bytes[2] = {0, 0};
     int64_t core_entries = 0;
