@@ -150,7 +150,7 @@ class ClockSampler:
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload,
 # precision and pass; see profiles/ for the command.  Entries are removed when
 # the kernel changes.
-TRAFFIC = {}
+TRAFFIC = {("helmholtz3d_n256", 2, "core@l2"): 6.00e9 + 645.72e6}
 
 
 def level_mode_bytes(info, w, nv, es):
