@@ -36,7 +36,7 @@ constexpr int MODE_NC = TB_MODE_NC;        // output columns per thread
 constexpr int MODE_MAXCH = 1 << MAXD;      // children of a group
 
 #ifndef TB_MODE_XB
-#define TB_MODE_XB 8
+#define TB_MODE_XB 6
 #endif
 constexpr int MODE_XB = TB_MODE_XB;        // input values of a column loaded before use
 constexpr int MODE_FIBER = 24;             // longest input fiber a Split's first mode keeps in registers
@@ -45,30 +45,50 @@ constexpr int MODE_FIBER = 24;             // longest input fiber a Split's firs
 // thread, i < OB, At row stride lda.  The column's inputs are loaded MODE_XB at
 // a time (all issued before the first use, so each thread keeps that many
 // loads in flight); each factor load (a warp-wide broadcast) feeds NC columns.
+template <class R, int OB, int NC, int XB>
+TB_DEV void mode_rows_chunk(cx<R> (&acc)[NC][OB], const cx<R> *__restrict__ At, int lda, int a0, int b, int m,
+                            const cx<R> (&x)[NC][XB]) {
+    const cx<R> *r = At + b * lda + a0;
+#pragma unroll
+    for (int t = 0; t < XB; ++t) {
+        if (b + t >= m) break;
+#pragma unroll
+        for (int i = 0; i < OB; i += 2) {
+            cx<R> u, w;
+            ld2(r + t * lda + i, u, w);
+#pragma unroll
+            for (int j = 0; j < NC; ++j) {
+                cmac(acc[j][i], u, x[j][t]);
+                cmac(acc[j][i + 1], w, x[j][t]);
+            }
+        }
+    }
+}
+
+template <class R, int NC, int XB, class LD>
+TB_DEV void mode_load_chunk(cx<R> (&x)[NC][XB], int b, int m, const LD &ld) {
+#pragma unroll
+    for (int t = 0; t < XB; ++t)
+#pragma unroll
+        for (int j = 0; j < NC; ++j) x[j][t] = (b + t < m) ? ld(j, b + t) : cx<R>{R(0), R(0)};
+}
+
+// acc[j][i] += sum_{b < m} At[b][a0 + i] x_j(b) for the NC columns j of a
+// thread, i < OB, At row stride lda.  The column's inputs are loaded MODE_XB at
+// a time into two register buffers: the next chunk's loads are in flight while
+// the current chunk is multiplied.  Each factor load (a warp-wide broadcast)
+// feeds NC columns.
 template <class R, int OB, int NC, class LD>
 TB_DEV void mode_rows(cx<R> (&acc)[NC][OB], const cx<R> *__restrict__ At, int lda, int a0, int m, const LD &ld) {
     constexpr int XB = MODE_XB;
-    for (int b = 0; b < m; b += XB) {
-        cx<R> x[NC][XB];
-#pragma unroll
-        for (int t = 0; t < XB; ++t)
-#pragma unroll
-            for (int j = 0; j < NC; ++j) x[j][t] = (b + t < m) ? ld(j, b + t) : cx<R>{R(0), R(0)};
-        const cx<R> *r = At + b * lda + a0;
-#pragma unroll
-        for (int t = 0; t < XB; ++t) {
-            if (b + t >= m) break;
-#pragma unroll
-            for (int i = 0; i < OB; i += 2) {
-                cx<R> u, w;
-                ld2(r + t * lda + i, u, w);
-#pragma unroll
-                for (int j = 0; j < NC; ++j) {
-                    cmac(acc[j][i], u, x[j][t]);
-                    cmac(acc[j][i + 1], w, x[j][t]);
-                }
-            }
-        }
+    cx<R> x0[NC][XB], x1[NC][XB];
+    mode_load_chunk<R, NC, XB>(x0, 0, m, ld);
+    for (int b = 0; b < m; b += 2 * XB) {
+        if (b + XB < m) mode_load_chunk<R, NC, XB>(x1, b + XB, m, ld);
+        mode_rows_chunk<R, OB, NC, XB>(acc, At, lda, a0, b, m, x0);
+        if (b + XB >= m) break;
+        if (b + 2 * XB < m) mode_load_chunk<R, NC, XB>(x0, b + 2 * XB, m, ld);
+        mode_rows_chunk<R, OB, NC, XB>(acc, At, lda, a0, b + XB, m, x1);
     }
 }
 
@@ -89,7 +109,10 @@ TB_DEV void stage_fac(cx<R> *dst, const cx<R> *__restrict__ src, int r, int c, b
 }
 
 template <class R, int IN, int OUT, int OB>
-__global__ void __launch_bounds__(MODE_THREADS) k_mode(const ModeArgs<R> a) {
+#ifndef TB_MODE_MINB
+#define TB_MODE_MINB 6   // complex64: resident blocks per SM the register allocation must allow
+#endif
+__global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? TB_MODE_MINB : 2) k_mode(const ModeArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<R> *As = reinterpret_cast<cx<R> *>(smraw);
     constexpr bool GROUP = (IN == MK_PARENTS || OUT == MK_PARENTS);
