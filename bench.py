@@ -320,6 +320,20 @@ def main():
         op.profile(False)
     stats = op.profile_stats()
     ms = max_over_ranks(ws, ms)
+    # the adjoint apply K^H on the same batch (graph replay, same step count)
+    v = torch.empty_like(f)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            op.apply_adjoint(f, prec, out=v)
+    stream.synchronize()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for _ in range(args.steps):
+            op.apply_adjoint(f, prec, out=v)
+        ev1.record(stream)
+    stream.synchronize()
+    ms_adj = max_over_ranks(ws, ev0.elapsed_time(ev1) / args.steps)
+    adjoint = {"value": ws * N * nv / (ms_adj * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_adj}
     value = ws * N * nv / (ms * 1e-3) / 1e9
     # kernel launches of one apply, counted from the per-pass event records
     launches_per_step = int(round(sum(s["kernels"] for s in stats) / max(args.steps, 1))) if stats else 0
@@ -379,7 +393,7 @@ def main():
                       "core_entries": info["core_entries"], "build_s": info["build_seconds"],
                       "l2": "inputs larger than L2 (no flush)", "graph": True,
                       "autotune_s": tune_s},
-           "roofline": roof, "passes": passes, "e2e": e2e,
+           "roofline": roof, "passes": passes, "adjoint": adjoint, "e2e": e2e,
            "gpu_launches": launches_per_step * args.steps}
 
     if rank == 0:
