@@ -74,3 +74,12 @@ def test_apply_rejects_null_handle(lib):
     assert lib.tb_apply(None, None, None, 1, 0, None) == 1
     assert lib.tb_apply_adjoint(None, None, None, 1, 0, None) == 1
     assert lib.tb_query(None, None) == 1
+
+
+def test_autotune_and_apply_reject_a_null_handle_without_touching_the_gpu(lib):
+    assert lib.tb_autotune(None, 1, tb.PREC_C64, None) == 1          # TB_EINVAL
+    assert b"handle" in lib.tb_last_error()
+    assert lib.tb_apply(None, None, None, 1, tb.PREC_C64, None) == 1
+    opt = tb._Options()
+    assert lib.tb_options_default(ctypes.byref(opt)) == 0
+    assert opt.autotune == 0                                           # off unless asked for
