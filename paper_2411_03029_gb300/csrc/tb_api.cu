@@ -949,6 +949,18 @@ tb_status pick_chunk(int d, const int *m, const int *o, int64_t nv, int64_t &nvc
     return TB_OK;
 }
 
+// Output rows per register tile of a mode launch: the instantiated values
+// (even, up to 16, and 18, 20, 24), and the built-in rule: the fewest chunks
+// of at most 24 rows, split evenly.
+bool mode_ob_valid(int ob) { return ob >= 2 && !(ob & 1) && (ob <= 20 || ob == 24); }
+int mode_ob_rule(int o) {
+    const int nch = (o + 23) / 24;
+    int ob = (o + nch - 1) / nch;
+    ob += ob & 1;
+    if (ob == 22) ob = 24;
+    return ob;
+}
+
 // One level pass as d mode-product launches (tb_mode.cu).  T holds the two
 // ping-pong buffers of the mode intermediates.
 template <class R>
@@ -1056,11 +1068,7 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
         const int64_t target = waves * (int64_t)g_num_sms;
         a.gsplit = std::min<int64_t>(a.ncb, std::max<int64_t>(1, (target + a.nblk - 1) / a.nblk));
         int ob = ob_set ? ob_set : tune[k].ob;
-        if (ob < 2 || ob > 16 || (ob & 1)) {   // built-in rule: fewest chunks of at most 16 rows
-            const int nch = (o[k] + 15) / 16;
-            ob = (o[k] + nch - 1) / nch;
-            ob += ob & 1;
-        }
+        if (!mode_ob_valid(ob)) ob = mode_ob_rule(o[k]);
         a.lda = (o[k] + ob - 1) / ob * ob;
         a.fsz = m[k] * a.lda;
         const int nfac = group ? (1 << d) : 1;
@@ -1510,7 +1518,8 @@ tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, cons
                         for (int nch = 1; nch <= 3; ++nch) {
                             int ob = (o[k] + nch - 1) / nch;
                             ob += ob & 1;
-                            if (ob < 2 || ob > 16) continue;
+                            if (ob == 22) ob = 24;
+                            if (!mode_ob_valid(ob)) continue;
                             bool dup = false;
                             for (int i = 0; i < nob; ++i) dup = dup || obs[i] == ob;
                             if (!dup) obs[nob++] = ob;

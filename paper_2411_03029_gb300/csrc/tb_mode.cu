@@ -112,7 +112,8 @@ template <class R, int IN, int OUT, int OB>
 #ifndef TB_MODE_MINB
 #define TB_MODE_MINB 6   // complex64: resident blocks per SM the register allocation must allow
 #endif
-__global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? TB_MODE_MINB : 2) k_mode(const ModeArgs<R> a) {
+__global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_MODE_MINB : 4) : 2)
+    k_mode(const ModeArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<R> *As = reinterpret_cast<cx<R> *>(smraw);
     constexpr bool GROUP = (IN == MK_PARENTS || OUT == MK_PARENTS);
@@ -399,6 +400,9 @@ cudaError_t launch_mode_ob(int ob, const ModeArgs<R> &a, cudaStream_t st) {
         case 12: fn = k_mode<R, IN, OUT, 12>; break;
         case 14: fn = k_mode<R, IN, OUT, 14>; break;
         case 16: fn = k_mode<R, IN, OUT, 16>; break;
+        case 18: fn = k_mode<R, IN, OUT, 18>; break;
+        case 20: fn = k_mode<R, IN, OUT, 20>; break;
+        case 24: fn = k_mode<R, IN, OUT, 24>; break;
         default: return cudaErrorInvalidValue;
     }
     cudaError_t e = set_smem_once((const void *)fn, a.smem);
