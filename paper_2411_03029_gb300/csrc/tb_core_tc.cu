@@ -26,7 +26,7 @@
 // with warp-specialised roles that meet at mbarriers:
 //   warp 0       streams the core K-chunks into STAGES shared-memory stages
 //                (cp.async.bulk, completion counted in bytes);
-//   warps 8..11  load the matching 32 x 16 input values (three chunks ahead,
+//   warps 8..11  load the matching 32 x 16 input values (CONV_AHEAD chunks ahead,
 //                through a build-time table of padded input positions), split
 //                them into BF16 pairs and write the B rows of the stage;
 //   warp 1       issues the MMAs of a chunk once both halves of its stage have
@@ -62,6 +62,10 @@ constexpr int EPI_WARP0 = 4;               // warps 4..7: one per TMEM lane quar
 constexpr int CONV_WARP0 = 8;              // warps 8..11
 constexpr int PAD_WARP0 = 2;               // warps 2..3
 constexpr int NEPI = 128, NCONV = 128, NPAD = 64;
+#ifndef TB_CONV_AHEAD
+#define TB_CONV_AHEAD 3
+#endif
+constexpr int CONV_AHEAD = TB_CONV_AHEAD;   // input chunks the converters keep in flight
 constexpr long long SPIN_LIMIT = 1ll << 26;
 
 TB_DEV uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -367,12 +371,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
             }
             load_pos();   // for the next call
         };
-        // three chunks of values in flight, in fixed registers (no copies of
-        // values that may still be loading)
-        cx<float> b0[4], b1[4], b2[4];
-        load_next(b0);
-        load_next(b1);
-        load_next(b2);
+        // CONV_AHEAD chunks of values in flight, in fixed registers (the loop
+        // below is unrolled, so no value that may still be loading is copied)
+        cx<float> xb[CONV_AHEAD][4];
+#pragma unroll
+        for (int u = 0; u < CONV_AHEAD; ++u) load_next(xb[u]);
         int64_t item = blockIdx.x, gi = 0;
         int kc = 0, nkc = item < a.nitems ? a.items[item].nkc : 0;
         bool ok = true;
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
             fence_proxy_async();   // generic-proxy writes -> visible to the MMA
             mbar_arrive(&xfull_bar[s]);
             ++gi;
-            load_next(x);   // the chunk three ahead
+            load_next(x);   // the chunk CONV_AHEAD ahead
             if (++kc >= nkc) {
                 kc = 0;
                 item += gridDim.x;
@@ -411,7 +414,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
             }
             return true;
         };
-        while (step(b0) && step(b1) && step(b2)) {
+        for (bool more = true; more;) {
+#pragma unroll
+            for (int u = 0; u < CONV_AHEAD; ++u)
+                if (more) more = step(xb[u]);
         }
         if (!ok) give_up();
     } else if (warp >= EPI_WARP0) {
