@@ -93,6 +93,13 @@ typedef struct {
     int device;            /* CUDA device ordinal; -1 = the current device */
     uint64_t seed;         /* seed of the proxy-row design (Sec. 2.1 proxy strategy) */
     int autotune;          /* 1 = run tb_autotune before the first apply of each (nv, precision) */
+    int sep_schedule;      /* separable handles (tb_autotune may replace it):
+                              0 = built-in rule (= 3),
+                              1 = per-mode passes, each thread's fiber in shared memory,
+                              2 = multi-mode tile passes in shared memory,
+                              3 = per-mode passes with the fiber in registers for every mode
+                                  whose ranks equal its leaf size (exact-rank chains,
+                                  e.g. the bit-reversed Fourier kernel), 1 for the others */
 } tb_options;
 
 typedef struct tb_plan *tb_handle;
@@ -207,7 +214,9 @@ tb_status tb_apply_noalloc(tb_handle h, const void *f, void *u, int64_t nv, int 
  *  - non-separable handles: for every level pass, side and mode, the output
  *    rows per register tile (even values up to 16) and the number of thread
  *    blocks per unit;
- *  - separable handles: per-mode fiber passes against multi-mode tile passes.
+ *  - separable handles: per-mode passes with shared-memory fibers, with
+ *    register-resident fibers (where the chain has the exact-rank form; see
+ *    tb_options.sep_schedule) and multi-mode tile passes.
  * Each candidate runs a few times on `cuda_stream` (CUDA-event timed); the
  * fastest is kept in the handle and used by every later apply (results are
  * identical up to the summation order of separable passes).  Allocates two

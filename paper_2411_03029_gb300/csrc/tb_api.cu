@@ -115,6 +115,7 @@ tb_status tb_options_default(tb_options *o) {
     o->device = -1;
     o->seed = 0x5eed;
     o->autotune = 0;
+    o->sep_schedule = 0;
     return TB_OK;
 }
 
@@ -448,6 +449,64 @@ HostStep conj_transpose(const HostStep &a) {
 
 }  // namespace
 
+// Register-resident form of mode k's chain (sepr_col): eligible when the
+// chain has N = C_b 4^Lc entries at every level, V and U^T are permutation
+// matrices (every row a single exact 1) and every other step's nonzeros lie
+// in the dense-block pattern.  Fills the load / store positions and the
+// dense coefficients (zero where the CSR step dropped an exact zero).
+static tb_status build_sep_reg(tb_plan *h, int k, const std::vector<HostStep> &st) {
+    const int lc = h->Lc, rk = (int)h->cb[k], N = rk << (2 * lc), nk = (int)h->n[k];
+    h->sepr_ok[k] = 0;
+    if (N != nk || N > SEPR_MAXN || (int)st.size() != 2 * lc + 3) return TB_OK;
+    if (!sep_reg_supported<float>(lc, rk) && !sep_reg_supported<double>(lc, rk)) return TB_OK;
+    for (const HostStep &s : st)
+        if (s.n_out != N || s.n_in != N) return TB_OK;
+    const std::complex<double> one(1.0, 0.0);
+    // V (first step): row e reads grid position ld[e]; U^T (last): row g reads entry e, so st[e] = g
+    std::vector<int> ld(N, -1), sto(N, -1), seen(N, 0), seen2(N, 0);
+    const HostStep &V = st.front(), &U = st.back();
+    for (int e = 0; e < N; ++e) {
+        if (V.rowptr[e + 1] - V.rowptr[e] != 1 || V.val[V.rowptr[e]] != one) return TB_OK;
+        const int c = V.col[V.rowptr[e]];
+        if (seen[c]++) return TB_OK;
+        ld[e] = c;
+        if (U.rowptr[e + 1] - U.rowptr[e] != 1 || U.val[U.rowptr[e]] != one) return TB_OK;
+        const int c2 = U.col[U.rowptr[e]];
+        if (seen2[c2]++) return TB_OK;
+        sto[c2] = e;
+    }
+    std::vector<std::complex<double>> coef((size_t)sepr_ncoef(lc, rk), std::complex<double>(0.0, 0.0));
+    for (int i = 0; i <= 2 * lc; ++i) {
+        const HostStep &S = st[(size_t)i + 1];
+        const int K = sepr_width(lc, rk, i), off = sepr_off(lc, rk, i);
+        for (int e = 0; e < N; ++e)
+            for (int j = S.rowptr[e]; j < S.rowptr[e + 1]; ++j) {
+                int pos = -1;
+                for (int q = 0; q < K && pos < 0; ++q)
+                    if (sepr_col(lc, rk, i, e, q) == S.col[j]) pos = q;
+                if (pos < 0) return TB_OK;   // a nonzero outside the dense-block pattern
+                coef[(size_t)(off + e * K + pos)] = S.val[j];
+            }
+    }
+    std::vector<c128> c64v(coef.size());
+    std::vector<c64> c32v(coef.size());
+    for (size_t i = 0; i < coef.size(); ++i) {
+        c64v[i] = c128{coef[i].real(), coef[i].imag()};
+        c32v[i] = c64{(float)coef[i].real(), (float)coef[i].imag()};
+    }
+    TB_TRY(dalloc(h, &h->sepr_coef64[k], (int64_t)coef.size()));
+    TB_TRY(dalloc(h, &h->sepr_coef32[k], (int64_t)coef.size()));
+    TB_CK(cudaMemcpy(h->sepr_coef64[k], c64v.data(), c64v.size() * sizeof(c128), cudaMemcpyHostToDevice));
+    TB_CK(cudaMemcpy(h->sepr_coef32[k], c32v.data(), c32v.size() * sizeof(c64), cudaMemcpyHostToDevice));
+    for (int e = 0; e < N; ++e) {
+        h->sepr_ld[k][e] = ld[(size_t)e];
+        h->sepr_st[k][e] = sto[(size_t)e];
+    }
+    h->sepr_rk[k] = rk;
+    h->sepr_ok[k] = 1;
+    return TB_OK;
+}
+
 // The per-mode chains of a separable handle: step matrices on the 1-D index
 // of mode k, assembled from the factor blocks (which depend on the mode-k
 // nodes only).  Source level l index: ((s 2^l + tau) 2^(Lc-l) + nu) R_l + a;
@@ -567,6 +626,7 @@ static tb_status build_sep_steps(tb_plan *h) {
             }
             st.push_back(b.s);
         }
+        TB_TRY(build_sep_reg(h, k, st));
         int mx = nk;
         for (auto &s : st) mx = std::max({mx, s.n_out, s.n_in});
         h->sep_maxext[k] = mx;
@@ -790,6 +850,7 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     }
     if (L % 2 != 0 || L < 0 || L >= TB_MAX_LEVELS || (nmin >> L) < 1)
         return fail(TB_EINVAL, "L must be even with n_k / 2^L >= 1");
+    if (opt.sep_schedule < 0 || opt.sep_schedule > 3) return fail(TB_EINVAL, "sep_schedule must be 0, 1, 2 or 3");
     int dev = opt.device;
     if (dev < 0) {
         if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "no CUDA device"); }
@@ -817,6 +878,7 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     }
     h->use_graphs = opt.use_graphs;
     h->autotune = opt.autotune;
+    h->sep_choice = opt.sep_schedule;
     h->proxy_rows = opt.proxy_rows;
     h->rank_max = opt.rank_max;
     h->seed = opt.seed;
@@ -1212,6 +1274,13 @@ const SepStep<double> *sepptr<double>(const tb_plan *h, int dir) { return h->sep
 template <>
 const SepStep<float> *sepptr<float>(const tb_plan *h, int dir) { return h->sep32[dir]; }
 
+template <class R>
+const cx<R> *sepr_coef(const tb_plan *h, int k);
+template <>
+const cx<double> *sepr_coef<double>(const tb_plan *h, int k) { return h->sepr_coef64[k]; }
+template <>
+const cx<float> *sepr_coef<float>(const tb_plan *h, int k) { return h->sepr_coef32[k]; }
+
 // Separable handle: per-mode chains applied in passes over up to three
 // consecutive modes (from the last mode down), ping-ponging full tensors.
 template <class R>
@@ -1222,23 +1291,61 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
     const int64_t limit = 96 * 1024;
     int64_t N = 1;
     for (int k = 0; k < d; ++k) N *= h->n[k];
-    // thread-per-fiber passes, one per mode, when every mode's chain fits a
+    // per-mode passes: register-resident chains where the mode has the
+    // exact-rank form, else thread-per-fiber passes when the chain fits a
     // shared-memory column of at least 32 threads per block
     {
         int threads[TB_MAX_D];
         size_t smem[TB_MAX_D];
+        bool use_reg[TB_MAX_D];
         bool fits = true;
         for (int k = 0; k < d && fits; ++k) {
+            int64_t inner = nv;
+            for (int j = k + 1; j < d; ++j) inner *= h->n[j];
+            use_reg[k] = (h->sep_choice == 0 || h->sep_choice == 3) && h->sepr_ok[k] &&
+                         sep_reg_supported<R>(h->Lc, h->sepr_rk[k]) && h->n[k] * inner < ((int64_t)1 << 31);
             const int64_t fixed = h->sep_npk[dir][k] * (int64_t)sizeof(SepNz<R>);
             int T = 256;
             while (T >= 32 && 2 * h->sep_maxext[k] * T * es + fixed > limit) T /= 2;
             threads[k] = T;
             smem[k] = (size_t)(2 * h->sep_maxext[k] * T * es + fixed + 16);
-            fits = T >= 32;
+            fits = use_reg[k] || T >= 32;
         }
         if (fits && h->sep_choice != 2) {
             int i = 0;
             for (int k = d - 1; k >= 0; --k, ++i) {
+                if (use_reg[k]) {
+                    SepRegArgs<R> a;
+                    std::memset(&a, 0, sizeof(a));
+                    a.lc = h->Lc;
+                    a.rk = h->sepr_rk[k];
+                    a.outer = 1;
+                    for (int j = 0; j < k; ++j) a.outer *= h->n[j];
+                    a.inner = nv;
+                    for (int j = k + 1; j < d; ++j) a.inner *= h->n[j];
+                    a.in = (const cx<R> *)(i == 0 ? in : B[(i - 1) & 1]);
+                    a.out = (cx<R> *)(k == 0 ? out : B[i & 1]);
+                    a.coef = sepr_coef<R>(h, k);
+                    for (int p = 0; p < h->n[k]; ++p) {
+                        a.ldo[p] = (int)(h->sepr_ld[k][p] * a.inner);
+                        a.sto[p] = (int)(h->sepr_st[k][p] * a.inner);
+                    }
+                    a.blocks = g_num_sms * 3;
+                    ProfRec r{"sep_reg", k, (int)adjoint, nullptr, nullptr, 0, 0.0};
+                    if (prof) {
+                        r.bytes = 2 * N * nv * es + h->sep_nnz[dir][k] * (es + 4);
+                        r.flops = 8.0 * (double)h->sep_nnz[dir][k] * (double)(N / h->n[k]) * (double)nv;
+                        TB_CK(cudaEventCreate(&r.e0));
+                        TB_CK(cudaEventCreate(&r.e1));
+                        TB_CK(cudaEventRecord(r.e0, st));
+                    }
+                    TB_CK(launch_sep_reg<R>(adjoint, a, st));
+                    if (prof) {
+                        TB_CK(cudaEventRecord(r.e1, st));
+                        h->prof.push_back(r);
+                    }
+                    continue;
+                }
                 SepFiberArgs<R> a;
                 std::memset(&a, 0, sizeof(a));
                 a.k = k;
@@ -1488,7 +1595,9 @@ tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, cons
     if (h->separable) {
         float best = 3.0e38f;
         int choice = 0;
-        for (int c = 1; c <= 2 && status == TB_OK; ++c) {
+        bool any_reg = false;
+        for (int k = 0; k < h->d; ++k) any_reg = any_reg || h->sepr_ok[k];
+        for (int c = 1; c <= (any_reg ? 3 : 2) && status == TB_OK; ++c) {
             h->sep_choice = c;
             float t = 0.f;
             status = time_it([&] { return run_chain<R>(h, false, uin, uout, nv, st, false, precision); }, t);

@@ -265,6 +265,72 @@ struct SepFiberArgs {
 template <class R>
 cudaError_t launch_sep_fiber(const SepFiberArgs<R> &a, cudaStream_t st);
 
+// Register-resident chains.  When every rank of mode k equals its leaf size
+// C_b (the bit-reversed uniform Fourier kernel, whose DFT blocks have exact
+// rank C_b), every level of the mode's 1-D chain has N = C_b 4^Lc entries, the
+// leaf interpolation V and the leaf U^T are permutation matrices (an ID that
+// keeps every column), and each remaining step is a fixed pattern of dense
+// blocks: W_l and P_l rows read 2 C_b inputs, core rows read C_b inputs.  The
+// pattern is a compile-time function of (Lc, C_b), so a thread keeps its whole
+// fiber in registers; V and U^T become the load and store positions.
+//   step st = 0 .. Lc-1 : W_{st+1}      (source transfers)
+//   step st = Lc        : core K_k
+//   step st = Lc+1 .. 2Lc: P_{2Lc+1-st} (target transfers)
+// Source level-l entry ((s 2^l + tau) 2^(Lc-l) + nu) C_b + a and target
+// level-l entry ((t 2^l + nu) 2^(Lc-l) + tau) C_b + a, as in the CSR steps.
+TB_HD constexpr int sepr_width(int lc, int rk, int st) { return st == lc ? rk : 2 * rk; }
+// input column j of output row e of forward step st
+TB_HD constexpr int sepr_col(int lc, int rk, int st, int e, int j) {
+    const int a = e % rk, r1 = e / rk;
+    if (st < lc) {   // W_l, l = st + 1: children 2 nu, 2 nu + 1 of source level l - 1, contiguous
+        const int l = st + 1;
+        const int nu = r1 & ((1 << (lc - l)) - 1), r2 = r1 >> (lc - l);
+        const int tau = r2 & ((1 << l) - 1), s = r2 >> l;
+        (void)a;
+        return ((((s << (l - 1)) + (tau >> 1)) << (lc - l + 1)) + 2 * nu) * rk + j;
+    }
+    if (st == lc) {  // core: output (t nb + s) C_b + a reads source mid-level entry (s nb + t) C_b + q
+        const int nb = 1 << lc, t = r1 / nb, s = r1 % nb;
+        return (s * nb + t) * rk + j;
+    }
+    // P_l, l = 2 Lc + 1 - st: output target level l - 1, inputs nu = 2 pn + c at level l
+    const int l = 2 * lc + 1 - st;
+    const int tp = r1 & ((1 << (lc - l + 1)) - 1), r2 = r1 >> (lc - l + 1);
+    const int pn = r2 & ((1 << (l - 1)) - 1), t = r2 >> (l - 1);
+    const int c = j / rk, q = j % rk;
+    return ((((t << l) + 2 * pn + c) << (lc - l)) + (tp >> 1)) * rk + q;
+}
+// offset of forward step st in the dense coefficient array (rows in order,
+// sepr_width entries per row, in the order of sepr_col's j)
+TB_HD constexpr int sepr_off(int lc, int rk, int st) {
+    const int n = rk << (2 * lc);
+    int o = 0;
+    for (int i = 0; i < st; ++i) o += n * sepr_width(lc, rk, i);
+    return o;
+}
+TB_HD constexpr int sepr_ncoef(int lc, int rk) { return sepr_off(lc, rk, 2 * lc + 1); }
+constexpr int SEPR_MAXN = 32;   // longest fiber kept in registers
+
+template <class R>
+struct SepRegArgs {
+    int lc, rk;                  // selects the instantiation
+    int64_t outer, inner;        // fiber (o, q): entry p at (o N + p) inner + q
+    const cx<R> *in;
+    cx<R> *out;
+    const cx<R> *coef;           // sepr_ncoef entries
+    // element offsets (grid position x inner) of level-0 entry p within a fiber:
+    // ldo for the source side (V and tree order), sto for the target side (U^T
+    // and tree order); N inner < 2^31
+    int ldo[SEPR_MAXN];
+    int sto[SEPR_MAXN];
+    int blocks;                  // grid size (0 = one thread per fiber)
+};
+
+template <class R>
+cudaError_t launch_sep_reg(bool adjoint, const SepRegArgs<R> &a, cudaStream_t st);
+template <class R>
+bool sep_reg_supported(int lc, int rk);
+
 enum class Pass { LeafIn, Split, Gather, LeafOut };
 
 template <class R>

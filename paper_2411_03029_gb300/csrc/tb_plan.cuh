@@ -113,10 +113,19 @@ struct tb_plan {
     int64_t sep_nnz[2][TB_MAX_D] = {{0}};
     int64_t sep_nidx[2][TB_MAX_D] = {{0}};   // row-pointer entries of a mode's steps
     int64_t sep_npk[2][TB_MAX_D] = {{0}};    // packed nonzero-stream entries of a mode's steps
+    // register-resident chains (see sepr_col): per mode, whether the chain has
+    // the exact-rank form, its rank, dense step coefficients and the grid
+    // positions of the level-0 source / target entries
+    int sepr_ok[TB_MAX_D] = {0};
+    int sepr_rk[TB_MAX_D] = {0};
+    tb::c128 *sepr_coef64[TB_MAX_D] = {nullptr};
+    tb::c64 *sepr_coef32[TB_MAX_D] = {nullptr};
+    int sepr_ld[TB_MAX_D][tb::SEPR_MAXN] = {{0}};
+    int sepr_st[TB_MAX_D][tb::SEPR_MAXN] = {{0}};
 
     // launch shapes chosen by tb_autotune: [complex64 / complex128][side][pass][level][mode]
     tb::ModeTune tune[2][2][4][TB_MAX_LEVELS][TB_MAX_D];
-    int sep_choice = 0;            // separable apply: 0 rule, 1 per-mode fiber passes, 2 multi-mode tile passes
+    int sep_choice = 0;            // separable apply: tb_options.sep_schedule
     int autotune = 0;              // tune at the first apply of each (nv, precision)
     std::vector<std::pair<int64_t, int>> tuned;   // (nv, precision) pairs tuned so far
     int64_t level_max = 0;         // largest level tensor, entries per RHS

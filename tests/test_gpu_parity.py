@@ -257,3 +257,34 @@ def test_config_radon2d_n256_sampled():
     assert rel(run(op, w, f, tb.PREC_C64, rows), ref) <= w.bound
     refv = oracle.workload_apply_adjoint(w, f, rows)
     assert rel(run(op, w, f, tb.PREC_C64, rows, adjoint=True), refv) <= w.bound
+
+
+# ------------------------------------------- register-resident separable chains
+@pytest.mark.parametrize("d,n,nv,precs", [(3, 16, 3, (tb.PREC_C64,)), (4, 8, 2, (tb.PREC_C64, tb.PREC_C128)),
+                                          (2, 32, 4, (tb.PREC_C64,)), (6, 4, 5, (tb.PREC_C64, tb.PREC_C128))])
+def test_separable_register_chains_match_shared_memory_fibers(d, n, nv, precs):
+    """With ranks equal to the leaf size (bit-reversed uniform Fourier, L = 2) the
+    register-resident chains apply the same steps as the shared-memory fiber
+    passes: both agree to rounding, and with the DFT identity."""
+    w = W.Workload(name="f", kind=W.FOURIER, d=d, n=n, tol=1e-8, nv=nv, precision=W.C64, bound=1e-5,
+                   rhs_seeds=tuple(range(nv)), samples=0, order=W.ORDER_BITREV, L=2)
+    f = W.rhs(w)
+    ref = oracle.fourier_fft(f.numpy(), d).reshape(-1, nv)
+    refv = oracle.workload_apply_adjoint(w, f)
+    ops = {s: tb.from_workload(w, sep_schedule=s) for s in (tb.SEP_FIBER, tb.SEP_REGISTER)}
+    for prec in precs:
+        out = {}
+        for s, op in ops.items():
+            op.profile(True)
+            out[s] = (run(op, w, f, prec), run(op, w, f, prec, adjoint=True))
+            names = {r["name"] for r in op.profile_stats()}
+            op.profile(False)
+            assert ("sep_reg" in names) == (s == tb.SEP_REGISTER), names
+        tight = 1e-12 if prec == tb.PREC_C128 else 2e-6
+        for s in out:
+            assert rel(out[s][0], ref) < tight
+            assert rel(out[s][1], refv) < tight
+        assert rel(out[tb.SEP_REGISTER][0], out[tb.SEP_FIBER][0]) < tight
+        assert rel(out[tb.SEP_REGISTER][1], out[tb.SEP_FIBER][1]) < tight
+    for op in ops.values():
+        op.close()
