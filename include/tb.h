@@ -50,10 +50,21 @@ typedef enum {
 
 /* Kernel families of the paper's numerical examples (Sec. 4). */
 typedef enum {
-    TB_KERNEL_FOURIER = 1,   /* K = exp(-2 pi i x.y)                        (Sec. 4.3) */
-    TB_KERNEL_HELMHOLTZ = 2, /* K = exp(i kappa |x-y|)/|x-y|, params[0]=kappa (Sec. 4.1) */
-    TB_KERNEL_RADON = 3      /* K = exp(2 pi i (x.xi + c(x)|xi|)),
-                                c(x) = params[0] + params[1] prod_k sin(2 pi x_k) (Sec. 4.2) */
+    TB_KERNEL_FOURIER = 1,   /* K = exp(-2 pi i x.y)                        (Sec. 4.3); any
+                                per-axis grids, e.g. random targets for the type-2
+                                non-uniform DFT of Sec. 4.3 */
+    TB_KERNEL_HELMHOLTZ = 2, /* K = exp(i kappa rho)/rho, rho = sqrt(|x-y|^2 + h^2),
+                                params[0] = kappa, params[1] = h >= 0: the offset of the
+                                source grid along an axis outside the d grid axes
+                                (h = 0: the cubes of Sec. 4.1; d = 2, h = 1: the
+                                parallel plates of Sec. 4.1) */
+    TB_KERNEL_RADON = 3,     /* K = exp(2 pi i (x.xi + c(x)|xi|)),
+                                c(x) = params[0] + params[1] prod_k sin(2 pi x_k) (Sec. 4.2;
+                                (3/100, 1/100) with d = 3 is Eq. randon3d) */
+    TB_KERNEL_RADON_ANISO = 4 /* d = 2 only: K = exp(2 pi i (x.xi + sqrt(c1^2 xi_1^2 + c2^2 xi_2^2))),
+                                c1 = params[0] + params[1] sin(2 pi x_1) sin(2 pi x_2),
+                                c2 = params[2] + params[3] cos(2 pi x_1) cos(2 pi x_2)
+                                (Sec. 4.2, Eq. randon2d: (2, 1, 2, 1) / 16) */
 } tb_kernel_kind;
 
 typedef enum {
@@ -138,7 +149,8 @@ tb_status tb_options_default(tb_options *opt);
  *   out     receives the handle (NULL on failure)
  * Factors are computed on the current CUDA device in FP64 (kernel phases,
  * column-pivoted QR, triangular solves) and stored in the precisions requested.
- * Errors: TB_EINVAL for bad sizes/pointers or coincident Helmholtz points,
+ * Errors: TB_EINVAL for bad sizes/pointers, coincident Helmholtz points, a
+ * negative Helmholtz offset h or an anisotropic Radon kernel with d != 2,
  * TB_ERANK if an ID needs more than the rank cap, TB_ENOMEM, TB_ECUDA.
  */
 tb_status tb_build(const tb_kernel *kernel, int d, const int64_t *n,

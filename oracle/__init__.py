@@ -184,9 +184,18 @@ def dense_matrix(kind, params, xs, ys) -> np.ndarray:
     if kind == 1:
         return np.exp(-2j * np.pi * (Xe * Ye).sum(-1))
     if kind == 2:
-        rho = np.sqrt(((Xe - Ye) ** 2).sum(-1))
+        h = params[1] if len(params) > 1 else 0.0
+        rho = np.sqrt(((Xe - Ye) ** 2).sum(-1) + h * h)
         return np.exp(1j * params[0] * rho) / rho
     if kind == 3:
         c = params[0] + params[1] * np.prod(np.sin(2 * np.pi * Xe), axis=-1)
         return np.exp(2j * np.pi * ((Xe * Ye).sum(-1) + c * np.sqrt((Ye ** 2).sum(-1))))
+    if kind == 4:
+        a1, b1, a2, b2 = params
+        s = np.sin(2 * np.pi * Xe)
+        c = np.cos(2 * np.pi * Xe)
+        c1 = a1 + b1 * s[..., 0] * s[..., 1]
+        c2 = a2 + b2 * c[..., 0] * c[..., 1]
+        phi = (Xe * Ye).sum(-1) + np.sqrt((c1 * Ye[..., 0]) ** 2 + (c2 * Ye[..., 1]) ** 2)
+        return np.exp(2j * np.pi * phi)
     raise ValueError(kind)

@@ -19,9 +19,16 @@
  *
  * Kernels (all evaluated in FP64 with libm, no range reduction):
  *   1 Fourier   K = exp(-2 pi i x.y)                       (Sec. 4.3, sign as configured)
- *   2 Helmholtz K = exp(i kappa rho) / rho, rho = |x - y|  (Sec. 4.1, outgoing sign as configured)
+ *   2 Helmholtz K = exp(i kappa rho) / rho,               (Sec. 4.1, outgoing sign as configured)
+ *               rho = sqrt(|x - y|^2 + h^2), par = (kappa, h): h is the distance
+ *               between the two grids along an axis outside the d grid axes
+ *               (h = 0: cubes; d = 2, h = 1: the parallel plates of Sec. 4.1)
  *   3 Radon     K = exp(2 pi i (x.xi + c(x)|xi|)),
  *               c(x) = a + b prod_k sin(2 pi x_k)          (Sec. 4.2, Eq. randon3d form)
+ *   4 Radon, anisotropic (d = 2, Sec. 4.2 Eq. randon2d):
+ *               K = exp(2 pi i (x.xi + sqrt(c1^2 xi_1^2 + c2^2 xi_2^2))),
+ *               c1 = a1 + b1 sin(2 pi x_1) sin(2 pi x_2), c2 = a2 + b2 cos(2 pi x_1) cos(2 pi x_2),
+ *               par = (a1, b1, a2, b2)
  */
 #include <complex.h>
 #include <math.h>
@@ -51,8 +58,15 @@ static double complex tbo_entry(int kind, const double *par, int d,
             double t = x[k] - y[k];
             r2 += t * t;
         }
-        double rho = sqrt(r2);
+        double rho = sqrt(r2 + par[1] * par[1]);
         return cexp(I * par[0] * rho) / rho;
+    }
+    if (kind == 4) {
+        if (d != 2) return 0.0;
+        double c1 = par[0] + par[1] * sin(TWO_PI * x[0]) * sin(TWO_PI * x[1]);
+        double c2 = par[2] + par[3] * cos(TWO_PI * x[0]) * cos(TWO_PI * x[1]);
+        double phi = x[0] * y[0] + x[1] * y[1] + sqrt(c1 * c1 * y[0] * y[0] + c2 * c2 * y[1] * y[1]);
+        return cexp(I * TWO_PI * phi);
     }
     if (kind == 3) {
         double xy = 0.0, yy = 0.0, s = 1.0;

@@ -808,9 +808,13 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     if (!out) return fail(TB_EINVAL, "out handle pointer is NULL");
     *out = nullptr;
     if (!kernel || !n || !grids) return fail(TB_EINVAL, "kernel, n and grids must be non-NULL");
-    if (kernel->kind < TB_KERNEL_FOURIER || kernel->kind > TB_KERNEL_RADON)
+    if (kernel->kind < TB_KERNEL_FOURIER || kernel->kind > TB_KERNEL_RADON_ANISO)
         return fail(TB_EINVAL, "unknown kernel kind " + std::to_string(kernel->kind));
     if (d < 1 || d > TB_MAX_D) return fail(TB_EINVAL, "d must be in [1, " + std::to_string(TB_MAX_D) + "]");
+    if (kernel->kind == TB_KERNEL_RADON_ANISO && d != 2)
+        return fail(TB_EINVAL, "the anisotropic Radon kernel is defined for d = 2");
+    if (kernel->kind == TB_KERNEL_HELMHOLTZ && !(kernel->params[1] >= 0.0))
+        return fail(TB_EINVAL, "Helmholtz offset h = params[1] must be >= 0");
     if (!(tol > 0.0 && tol < 1.0)) return fail(TB_EINVAL, "tol must be in (0, 1)");
     tb_options opt;
     tb_options_default(&opt);
@@ -825,7 +829,7 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     if (opt.rank_max <= 0) opt.rank_max = 32;
     if (opt.rank_max > id_max_columns() / 2) return fail(TB_EINVAL, "rank_max must be <= 32");
     // coincident source/target points make the Helmholtz kernel singular
-    if (kernel->kind == TB_KERNEL_HELMHOLTZ) {
+    if (kernel->kind == TB_KERNEL_HELMHOLTZ && kernel->params[1] == 0.0) {
         bool all_axes_meet = true;
         for (int k = 0; k < d && all_axes_meet; ++k) {
             std::vector<double> xa(grids->x[k], grids->x[k] + n[k]), ya(grids->y[k], grids->y[k] + n[k]);
@@ -885,7 +889,10 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     h->rank_min = 1 << 30;
     h->ks.kind = kernel->kind;
     for (int i = 0; i < 4; ++i) h->ks.p[i] = kernel->params[i];
-    if (kernel->kind == TB_KERNEL_HELMHOLTZ) h->ks.p[1] = kernel->params[0] / (2.0 * M_PI);
+    if (kernel->kind == TB_KERNEL_HELMHOLTZ) {
+        h->ks.p[1] = kernel->params[1] * kernel->params[1];
+        h->ks.p[2] = kernel->params[0] / (2.0 * M_PI);
+    }
     for (int k = 0; k < d; ++k) {
         h->n[k] = n[k];
         h->cb[k] = n[k] >> L;

@@ -60,8 +60,9 @@ TB_DEV void ld2(const cx<double> *p, cx<double> &a, cx<double> &b) {
 }
 
 // ---------------------------------------------------------------- kernels
-// Kernel descriptor as seen by device code.  For HELMHOLTZ, p[1] holds
-// kappa / (2 pi) so that the phase is formed in cycles.
+// Kernel descriptor as seen by device code.  For HELMHOLTZ, p[1] holds the
+// squared perpendicular offset h^2 and p[2] holds kappa / (2 pi), so that the
+// phase is formed in cycles.
 struct KernelSpec {
     int kind;
     double p[4];
@@ -86,12 +87,25 @@ TB_DEV c128 eval_kernel(const KernelSpec &ks, int d, const double *x, const doub
             double t = x[k] - y[k];
             r2 = fma(t, t, r2);
         }
-        double rho = sqrt(r2);
-        double ph = ks.p[1] * rho;
+        double rho = sqrt(r2 + ks.p[1]);
+        double ph = ks.p[2] * rho;
         ph -= rint(ph);
         sincospi(2.0 * ph, &s, &c);
         double inv = 1.0 / rho;
         return {c * inv, s * inv};
+    } else if (ks.kind == TB_KERNEL_RADON_ANISO) {
+        // exp(2 pi i (x.xi + sqrt(c1^2 xi_1^2 + c2^2 xi_2^2))), d = 2
+        const double s1 = sinpi(2.0 * x[0]), s2 = sinpi(2.0 * x[1]);
+        const double o1 = cospi(2.0 * x[0]), o2 = cospi(2.0 * x[1]);
+        const double c1 = ks.p[0] + ks.p[1] * s1 * s2, c2 = ks.p[2] + ks.p[3] * o1 * o2;
+        const double a1 = c1 * y[0], a2 = c2 * y[1];
+        double xy = fma(x[0], y[0], x[1] * y[1]);
+        double ph = xy - rint(xy);
+        double ph2 = sqrt(fma(a1, a1, a2 * a2));
+        ph2 -= rint(ph2);
+        ph += ph2;
+        sincospi(2.0 * ph, &s, &c);
+        return {c, s};
     } else {
         // exp(2 pi i (x.xi + c(x) |xi|)),  c(x) = a + b prod_k sin(2 pi x_k)
         double xy = 0.0, yy = 0.0, sp = 1.0;

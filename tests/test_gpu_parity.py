@@ -288,3 +288,24 @@ def test_separable_register_chains_match_shared_memory_fibers(d, n, nv, precs):
         assert rel(out[tb.SEP_REGISTER][1], out[tb.SEP_FIBER][1]) < tight
     for op in ops.values():
         op.close()
+
+
+# ------------------------------------------- the paper's other kernel families
+@pytest.mark.parametrize("name", ["plates2d_n64", "radon2d_aniso_n64", "radon3d_n32", "nudft3d_n16"])
+def test_other_paper_kernels(name):
+    """Parallel plates (Sec. 4.1), anisotropic 2-D and 3-D Radon (Sec. 4.2) and
+    the type-2 non-uniform DFT (Sec. 4.3): the butterfly's error against the
+    direct sum stays within 10 eps in FP64 and within the bound in complex64,
+    forward and adjoint (complex64: FP32 rounding, bound 1e-5)."""
+    w = W.WORKLOADS[name]
+    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C128))
+    info = op.info()
+    assert info["separable"] == (1 if w.kind == W.FOURIER else 0)
+    f = W.rhs(w)
+    rows = W.sample_targets(w) if w.samples else None
+    ref = oracle.workload_apply(w, f, rows)
+    refv = oracle.workload_apply_adjoint(w, f, rows)
+    for prec, bound in ((tb.PREC_C128, 10 * w.tol), (tb.PREC_C64, max(w.bound, 10 * w.tol, 1e-5))):
+        assert rel(run(op, w, f, prec, rows), ref) < bound, prec
+        assert rel(run(op, w, f, prec, rows, adjoint=True), refv) < bound, prec
+    op.close()

@@ -92,7 +92,8 @@ def test_radon_constant_c_is_modulated_inverse_dft():
 
 @pytest.mark.parametrize("kind,params,d,n", [
     (W.FOURIER, (), 2, 8), (W.HELMHOLTZ, (2 * math.pi * 3,), 3, 4),
-    (W.RADON, (2 / 16, 1 / 16), 2, 8), (W.RADON, (3 / 100, 1 / 100), 3, 4)])
+    (W.RADON, (2 / 16, 1 / 16), 2, 8), (W.RADON, (3 / 100, 1 / 100), 3, 4),
+    (W.HELMHOLTZ, (2 * math.pi * 3, 0.7), 2, 6), (W.RADON_ANISO, (2 / 16, 1 / 16, 2 / 16, 1 / 16), 2, 8)])
 def test_direct_sum_matches_dense_bruteforce(kind, params, d, n):
     xs, ys = _grid(kind, d, n, off=2.0)
     f = _rand((n,) * d + (2,), 21)
@@ -106,7 +107,8 @@ def test_direct_sum_matches_dense_bruteforce(kind, params, d, n):
 
 
 @pytest.mark.parametrize("kind,params,d,n", [
-    (W.FOURIER, (), 2, 8), (W.HELMHOLTZ, (2 * math.pi * 4,), 3, 6), (W.RADON, (2 / 16, 1 / 16), 2, 10)])
+    (W.FOURIER, (), 2, 8), (W.HELMHOLTZ, (2 * math.pi * 4,), 3, 6), (W.RADON, (2 / 16, 1 / 16), 2, 10),
+    (W.HELMHOLTZ, (2 * math.pi * 4, 1.0), 2, 9), (W.RADON_ANISO, (2 / 16, 1 / 16, 2 / 16, 1 / 16), 2, 10)])
 def test_adjoint_identity(kind, params, d, n):
     xs, ys = _grid(kind, d, n, off=2.0)
     f = _rand((n,) * d + (1,), 31)
@@ -142,6 +144,45 @@ def test_delta_input_returns_kernel_column(kind, params):
     assert np.allclose(u, col, rtol=0, atol=1e-14)
 
 
+def test_plates_offset_is_a_third_axis():
+    # d = 2 grids at perpendicular distance h (Sec. 4.1 plates) = the 3-D kernel on
+    # grids with a one-point third axis: x_3 = 0, y_3 = h
+    n, kappa, h = 7, 2 * math.pi * 3, 1.0
+    xs, ys = _grid(W.HELMHOLTZ, 2, n, off=0.0)
+    f = _rand((n, n, 2), 61)
+    u2 = oracle.apply(W.HELMHOLTZ, (kappa, h), xs, ys, f)
+    u3 = oracle.apply(W.HELMHOLTZ, (kappa,), xs + [np.zeros(1)], ys + [np.full(1, h)], f.reshape(n, n, 1, 2))
+    assert _rel(u2, u3) < 1e-14
+
+
+def test_anisotropic_radon_with_equal_constant_speeds_is_isotropic():
+    # b1 = b2 = 0 and a1 = a2 = a: sqrt(a^2 xi_1^2 + a^2 xi_2^2) = a |xi| (Eq. randon2d -> randon3d form)
+    n, a = 12, 0.2
+    xs, ys = _grid(W.RADON, 2, n)
+    f = _rand((n, n, 2), 62)
+    ua = oracle.apply(W.RADON_ANISO, (a, 0.0, a, 0.0), xs, ys, f)
+    ui = oracle.apply(W.RADON, (a, 0.0), xs, ys, f)
+    assert _rel(ua, ui) < 1e-13
+    # and the speeds act per axis: c2 alone modulates xi_2 only
+    ub = oracle.apply(W.RADON_ANISO, (0.0, 0.0, a, 0.0), xs, ys, f).reshape(f.shape)
+    Y = np.stack(np.meshgrid(*ys, indexing="ij"), -1)
+    mod = np.exp(2j * math.pi * a * np.abs(Y[..., 1]))[..., None]
+    assert _rel(ub, oracle.fourier_fft(f * mod, 2, sign=+1)) < 1e-12
+
+
+def test_nonuniform_fourier_is_a_product_of_1d_transforms():
+    # type-2 non-uniform DFT (Sec. 4.3): the kernel is separable, so u is f
+    # contracted with one 1-D matrix exp(-2 pi i x_k y_k) per axis
+    w = W.WORKLOADS["nudft3d_n16"]
+    w = W.Workload(**{**w.__dict__, "n": 6, "nv": 2})
+    xs, ys = W.grids(w)
+    assert all(np.all(np.diff(x) > 0) and x[0] >= 0 and x[-1] < 1 for x in xs)
+    f = _rand((6, 6, 6, 2), 63)
+    M = [np.exp(-2j * math.pi * np.outer(xs[k], ys[k])) for k in range(3)]
+    ref = np.einsum("ai,bj,ck,ijkv->abcv", M[0], M[1], M[2], f).reshape(-1, 2)
+    assert _rel(oracle.apply(W.FOURIER, (), xs, ys, f), ref) < 1e-13
+
+
 def test_sampled_rows_match_full_output():
     w = W.small("helmholtz3d_n64", 8)
     f = W.rhs(w, nv=2).numpy()
@@ -167,7 +208,8 @@ def test_rhs_columns_are_independent():
 
 def test_workload_definitions():
     assert set(W.WORKLOADS) == {"fourier2d_n64", "helmholtz3d_n64", "helmholtz3d_n256",
-                                "radon2d_n256", "fourier6d_n16"}
+                                "radon2d_n256", "fourier6d_n16", "plates2d_n64", "radon2d_aniso_n64",
+                                "radon3d_n32", "nudft3d_n16"}
     w = W.WORKLOADS["helmholtz3d_n256"]
     xs, ys = W.grids(w)
     assert ys[0][0] == 2.0 and ys[1][0] == 0.0 and xs[2][-1] == 255 / 256

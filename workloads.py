@@ -5,11 +5,13 @@ holds none of the method's arithmetic: only grid coordinates, kernel
 parameters, seeded right-hand sides and seeded sample sets.  Kernel formulas
 live separately in the oracle (plain C) and in the CUDA library.
 
-The five workloads follow the paper's numerical examples (Sec. 4): uniform
+The workloads follow the paper's numerical examples (Sec. 4): uniform
 DFTs (Sec. 4.3), Green's functions of the Helmholtz equation between two
 separated unit cubes (Sec. 4.1) and a 2-D generalized Radon transform
 (Sec. 4.2), with the sizes, tolerances and precisions of the benchmark
-configurations.  The paper evaluates on analytic kernels only, so these
+configurations; plus, at test sizes, the parallel plates of Sec. 4.1, the
+anisotropic 2-D and the 3-D Radon transforms of Sec. 4.2 and the type-2
+non-uniform DFT of Sec. 4.3.  The paper evaluates on analytic kernels only, so these
 synthetic inputs are the paper's workload shapes; no dataset is involved.
 """
 from __future__ import annotations
@@ -24,6 +26,7 @@ import torch
 FOURIER = 1      # K(x, y) = exp(-2 pi i x.y)
 HELMHOLTZ = 2    # K(x, y) = exp(i kappa |x - y|) / |x - y|
 RADON = 3        # K(x, xi) = exp(2 pi i (x.xi + c(x) |xi|)),  c(x) = a + b prod_k sin(2 pi x_k)
+RADON_ANISO = 4  # d = 2: K(x, xi) = exp(2 pi i (x.xi + sqrt(c1^2 xi_1^2 + c2^2 xi_2^2)))
 
 # apply precisions (include/tb.h: TB_PREC_*)
 C128 = 0
@@ -50,6 +53,7 @@ class Workload:
     order: int = ORDER_NATURAL
     L: int = -1               # level count; -1 lets the planner choose
     src_offset: tuple = ()    # per-axis offset of the source grid (Helmholtz cubes)
+    target_seed: int = -1     # >= 0: sorted uniform random targets on [0,1) per axis (type-2 NUDFT)
     description: str = ""
 
     @property
@@ -84,6 +88,28 @@ WORKLOADS = {
         name="radon2d_n256", kind=RADON, d=2, n=256, tol=1e-6, nv=1, precision=C64,
         bound=1e-4, params=(2.0 / 16.0, 1.0 / 16.0), rhs_seeds=(1,), samples=4096, L=6,
         description="d=2 Radon exp(2 pi i (x.xi + c(x)|xi|)), n=256, c64, autograd"),
+    # The paper's other examples at test sizes (Secs. 4.1-4.3), parity cases:
+    # Green's function between two parallel unit plates a distance 1 apart
+    # (params (kappa, h)), 4 points per wavelength: 2 pi n / kappa = 4.
+    "plates2d_n64": _wl(
+        name="plates2d_n64", kind=HELMHOLTZ, d=2, n=64, tol=1e-6, nv=2, precision=C64,
+        bound=1e-5, params=(math.pi * 64 / 2, 1.0), rhs_seeds=(0, 1), samples=0, L=4,
+        description="d=2 Helmholtz between parallel plates at distance 1, n=64, 4 points per wavelength"),
+    # 2-D Radon transform with the anisotropic phase of Eq. randon2d.
+    "radon2d_aniso_n64": _wl(
+        name="radon2d_aniso_n64", kind=RADON_ANISO, d=2, n=64, tol=1e-6, nv=2, precision=C64,
+        bound=1e-5, params=(2 / 16, 1 / 16, 2 / 16, 1 / 16), rhs_seeds=(0, 1), samples=0, L=4,
+        description="d=2 Radon, phase x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2), n=64"),
+    # 3-D Radon transform of Eq. randon3d: c(x) = (3 + prod_k sin(2 pi x_k)) / 100.
+    "radon3d_n32": _wl(
+        name="radon3d_n32", kind=RADON, d=3, n=32, tol=1e-6, nv=2, precision=C64,
+        bound=1e-5, params=(3 / 100, 1 / 100), rhs_seeds=(0, 1), samples=512, L=2,
+        description="d=3 Radon, c(x) = (3 + prod sin(2 pi x_k))/100, n=32"),
+    # Type-2 non-uniform DFT: random targets on [0,1)^3, integer frequencies.
+    "nudft3d_n16": _wl(
+        name="nudft3d_n16", kind=FOURIER, d=3, n=16, tol=1e-8, nv=2, precision=C128,
+        bound=1e-7, rhs_seeds=(0, 1), samples=0, order=ORDER_BITREV, L=2, target_seed=11,
+        description="d=3 type-2 non-uniform DFT, sorted random targets, n=16"),
     # d=6 uniform DFT, 16 points per direction, 8 right-hand sides.
     "fourier6d_n16": _wl(
         name="fourier6d_n16", kind=FOURIER, d=6, n=16, tol=1e-6, nv=8, precision=C64,
@@ -107,12 +133,17 @@ def small(name: str, n: int, nv: int | None = None, **kw) -> Workload:
 def grids(w: Workload):
     """Per-axis coordinates (xs, ys): lists of d float64 arrays of length n.
 
-    Targets x_k[i] = i/n on [0,1).  Sources: for FOURIER and RADON the integer
-    grid y_k[j] = j - n/2 on [-n/2, n/2); for HELMHOLTZ y_k[j] = off_k + j/n.
+    Targets x_k[i] = i/n on [0,1) (or sorted seeded uniform random points on
+    [0,1) when target_seed >= 0).  Sources: for FOURIER and the RADON kinds the
+    integer grid y_k[j] = j - n/2 on [-n/2, n/2); for HELMHOLTZ
+    y_k[j] = off_k + j/n (a perpendicular offset h is a kernel parameter).
     """
     n = w.n
     i = np.arange(n, dtype=np.float64)
     xs = [i / n for _ in range(w.d)]
+    if w.target_seed >= 0:
+        rng = np.random.default_rng(w.target_seed)
+        xs = [np.sort(rng.random(n)) for _ in range(w.d)]
     if w.kind == HELMHOLTZ:
         off = w.src_offset or (0.0,) * w.d
         ys = [off[k] + i / n for k in range(w.d)]
