@@ -51,6 +51,8 @@ def parse():
     p.add_argument("--err-samples", type=int, default=16)
     p.add_argument("--profile-only", action="store_true", help="eager applies only (for ncu)")
     p.add_argument("--n", type=int, default=None, help="points per axis of a reduced-size copy (profiling)")
+    p.add_argument("--sep-schedule", type=int, default=0,
+                   help="separable handles: tb_options.sep_schedule (0 rule; the tuner may replace it)")
     return p.parse_args()
 
 
@@ -267,7 +269,8 @@ def main():
     w = workload(args)
     prec = args.precision if args.precision is not None else w.precision
     mask = (1 << prec) | ((1 << tb.PREC_C128) if not args.no_fp64 else 0)
-    op = tb.from_workload(w, precisions=mask, use_graphs=not args.profile_only, precision=prec)
+    op = tb.from_workload(w, precisions=mask, use_graphs=not args.profile_only, precision=prec,
+                          sep_schedule=args.sep_schedule)
     info = op.info()
     nv = w.nv
     tune_s = None

@@ -108,9 +108,15 @@ typedef struct {
                               0 = built-in rule (= 3),
                               1 = per-mode passes, each thread's fiber in shared memory,
                               2 = multi-mode tile passes in shared memory,
-                              3 = per-mode passes with the fiber in registers for every mode
-                                  whose ranks equal its leaf size (exact-rank chains,
-                                  e.g. the bit-reversed Fourier kernel), 1 for the others */
+                              3 = per-mode passes with the fibers in registers for every
+                                  mode whose ranks equal its leaf size (exact-rank chains,
+                                  e.g. the bit-reversed Fourier kernel), 1 for the others;
+                                  complex64 uses paired FP32 FMAs, two fibers per thread,
+                              4 = as 3, with consecutive exact-rank modes fused in pairs
+                                  through a shared-memory tile (half the HBM passes),
+                              5 = as 3 with scalar FMAs, one fiber per thread and the
+                                  next fiber's loads in flight,
+                              6 = as 3 with one fiber per thread (4 resident blocks per SM) */
 } tb_options;
 
 typedef struct tb_plan *tb_handle;

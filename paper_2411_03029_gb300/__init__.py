@@ -23,7 +23,7 @@ TB_MAX_LEVELS = 16
 
 KERNEL_FOURIER, KERNEL_HELMHOLTZ, KERNEL_RADON = 1, 2, 3
 PREC_C128, PREC_C64, PREC_C64_SPLITBF16 = 0, 1, 2
-SEP_RULE, SEP_FIBER, SEP_TILE, SEP_REGISTER = 0, 1, 2, 3
+SEP_RULE, SEP_FIBER, SEP_TILE, SEP_REGISTER, SEP_REGISTER_PAIRS, SEP_REGISTER_SCALAR, SEP_REGISTER_ONE = range(7)
 ORDER_AUTO, ORDER_NATURAL, ORDER_BITREV = -1, 0, 1
 
 STATUS = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "TB_ERANK",

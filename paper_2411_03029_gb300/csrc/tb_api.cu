@@ -498,6 +498,15 @@ static tb_status build_sep_reg(tb_plan *h, int k, const std::vector<HostStep> &s
     TB_TRY(dalloc(h, &h->sepr_coef32[k], (int64_t)coef.size()));
     TB_CK(cudaMemcpy(h->sepr_coef64[k], c64v.data(), c64v.size() * sizeof(c128), cudaMemcpyHostToDevice));
     TB_CK(cudaMemcpy(h->sepr_coef32[k], c32v.data(), c32v.size() * sizeof(c64), cudaMemcpyHostToDevice));
+    for (int dir = 0; dir < 2; ++dir) {
+        std::vector<float4> f4(coef.size());
+        for (size_t i = 0; i < coef.size(); ++i) {
+            const float re = (float)coef[i].real(), im = (float)coef[i].imag();
+            f4[i] = make_float4(re, re, im, dir ? -im : im);
+        }
+        TB_TRY(dalloc(h, &h->sepr_cf4[dir][k], (int64_t)f4.size()));
+        TB_CK(cudaMemcpy(h->sepr_cf4[dir][k], f4.data(), f4.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    }
     for (int e = 0; e < N; ++e) {
         h->sepr_ld[k][e] = ld[(size_t)e];
         h->sepr_st[k][e] = sto[(size_t)e];
@@ -854,7 +863,7 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     }
     if (L % 2 != 0 || L < 0 || L >= TB_MAX_LEVELS || (nmin >> L) < 1)
         return fail(TB_EINVAL, "L must be even with n_k / 2^L >= 1");
-    if (opt.sep_schedule < 0 || opt.sep_schedule > 3) return fail(TB_EINVAL, "sep_schedule must be 0, 1, 2 or 3");
+    if (opt.sep_schedule < 0 || opt.sep_schedule > 6) return fail(TB_EINVAL, "sep_schedule must be in [0, 6]");
     int dev = opt.device;
     if (dev < 0) {
         if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "no CUDA device"); }
@@ -1309,7 +1318,7 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
         for (int k = 0; k < d && fits; ++k) {
             int64_t inner = nv;
             for (int j = k + 1; j < d; ++j) inner *= h->n[j];
-            use_reg[k] = (h->sep_choice == 0 || h->sep_choice == 3) && h->sepr_ok[k] &&
+            use_reg[k] = h->sep_choice != 1 && h->sep_choice != 2 && h->sepr_ok[k] &&
                          sep_reg_supported<R>(h->Lc, h->sepr_rk[k]) && h->n[k] * inner < ((int64_t)1 << 31);
             const int64_t fixed = h->sep_npk[dir][k] * (int64_t)sizeof(SepNz<R>);
             int T = 256;
@@ -1321,6 +1330,54 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
         if (fits && h->sep_choice != 2) {
             int i = 0;
             for (int k = d - 1; k >= 0; --k, ++i) {
+                if (h->sep_choice == 4 && k > 0 && use_reg[k] && use_reg[k - 1] &&
+                    h->sepr_rk[k] == h->sepr_rk[k - 1] && h->n[k] == h->n[k - 1]) {
+                    // modes k - 1 and k fused in one pass
+                    SepReg2Args<R> a;
+                    std::memset(&a, 0, sizeof(a));
+                    const int nk = (int)h->n[k];
+                    a.lc = h->Lc;
+                    a.rk = h->sepr_rk[k];
+                    a.outer = 1;
+                    for (int j = 0; j < k - 1; ++j) a.outer *= h->n[j];
+                    a.inner = nv;
+                    for (int j = k + 1; j < d; ++j) a.inner *= h->n[j];
+                    int lq = 0;
+                    while ((2 << lq) * nk <= 128 && ((int64_t)2 << lq) <= a.inner) ++lq;
+                    a.lq = lq;
+                    a.q = 1 << lq;
+                    a.nchunks = (a.inner + a.q - 1) / a.q;
+                    a.in = (const cx<R> *)(i == 0 ? in : B[(i - 1) & 1]);
+                    a.out = (cx<R> *)(k - 1 == 0 ? out : B[i & 1]);
+                    a.coef_a = sepr_coef<R>(h, k - 1);
+                    a.coef_b = sepr_coef<R>(h, k);
+                    a.cf4_a = h->sepr_cf4[dir][k - 1];
+                    a.cf4_b = h->sepr_cf4[dir][k];
+                    for (int p = 0; p < nk; ++p) {
+                        a.ld_a[p] = h->sepr_ld[k - 1][p];
+                        a.st_a[p] = h->sepr_st[k - 1][p];
+                        a.ld_b[p] = h->sepr_ld[k][p];
+                        a.st_b[p] = h->sepr_st[k][p];
+                    }
+                    ProfRec r{"sep_reg2", k - 1, (int)adjoint, nullptr, nullptr, 0, 0.0};
+                    if (prof) {
+                        r.bytes = 2 * N * nv * es;
+                        for (int j = k - 1; j <= k; ++j) {
+                            r.bytes += h->sep_nnz[dir][j] * (es + 4);
+                            r.flops += 8.0 * (double)h->sep_nnz[dir][j] * (double)(N / h->n[j]) * (double)nv;
+                        }
+                        TB_CK(cudaEventCreate(&r.e0));
+                        TB_CK(cudaEventCreate(&r.e1));
+                        TB_CK(cudaEventRecord(r.e0, st));
+                    }
+                    TB_CK(launch_sep_reg2<R>(adjoint, a, st));
+                    if (prof) {
+                        TB_CK(cudaEventRecord(r.e1, st));
+                        h->prof.push_back(r);
+                    }
+                    --k;
+                    continue;
+                }
                 if (use_reg[k]) {
                     SepRegArgs<R> a;
                     std::memset(&a, 0, sizeof(a));
@@ -1333,6 +1390,7 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
                     a.in = (const cx<R> *)(i == 0 ? in : B[(i - 1) & 1]);
                     a.out = (cx<R> *)(k == 0 ? out : B[i & 1]);
                     a.coef = sepr_coef<R>(h, k);
+                    a.cf4 = h->sepr_cf4[dir][k];
                     for (int p = 0; p < h->n[k]; ++p) {
                         a.ldo[p] = (int)(h->sepr_ld[k][p] * a.inner);
                         a.sto[p] = (int)(h->sepr_st[k][p] * a.inner);
@@ -1346,7 +1404,7 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
                         TB_CK(cudaEventCreate(&r.e1));
                         TB_CK(cudaEventRecord(r.e0, st));
                     }
-                    TB_CK(launch_sep_reg<R>(adjoint, a, st));
+                    TB_CK(launch_sep_reg<R>(adjoint, h->sep_choice == 5 ? 1 : h->sep_choice == 6 ? 2 : 0, a, st));
                     if (prof) {
                         TB_CK(cudaEventRecord(r.e1, st));
                         h->prof.push_back(r);
@@ -1604,7 +1662,7 @@ tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, cons
         int choice = 0;
         bool any_reg = false;
         for (int k = 0; k < h->d; ++k) any_reg = any_reg || h->sepr_ok[k];
-        for (int c = 1; c <= (any_reg ? 3 : 2) && status == TB_OK; ++c) {
+        for (int c = 1; c <= (any_reg ? 6 : 2) && status == TB_OK; ++c) {
             h->sep_choice = c;
             float t = 0.f;
             status = time_it([&] { return run_chain<R>(h, false, uin, uout, nv, st, false, precision); }, t);

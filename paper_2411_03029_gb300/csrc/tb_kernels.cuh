@@ -318,6 +318,10 @@ struct SepRegArgs {
     const cx<R> *in;
     cx<R> *out;
     const cx<R> *coef;           // sepr_ncoef entries
+    // complex64 paired-FMA form: per coefficient (re, re, im, im) for the
+    // forward apply, (re, re, im, -im) for the adjoint (the host passes the
+    // direction's array)
+    const float4 *cf4;
     // element offsets (grid position x inner) of level-0 entry p within a fiber:
     // ldo for the source side (V and tree order), sto for the target side (U^T
     // and tree order); N inner < 2^31
@@ -326,8 +330,32 @@ struct SepRegArgs {
     int blocks;                  // grid size (0 = one thread per fiber)
 };
 
+// variant (complex64): 0 = paired FP32 FMAs, two fibers per thread;
+// 1 = scalar FMAs, one fiber per thread with the next fiber's loads in flight.
+// Complex128 has the scalar form only.
 template <class R>
-cudaError_t launch_sep_reg(bool adjoint, const SepRegArgs<R> &a, cudaStream_t st);
+cudaError_t launch_sep_reg(bool adjoint, int variant, const SepRegArgs<R> &a, cudaStream_t st);
+
+// Two consecutive exact-rank modes ka = kb - 1 and kb with the same N, fused
+// in one pass: a block takes a tile (o, all i_ka, all i_kb, q chunk of Q),
+// applies mode kb to its fibers with the result written to shared memory in
+// grid order, then mode ka to the tile's other fibers.  Element
+// (o, i_ka, i_kb, q) sits at ((o N + i_ka) N + i_kb) inner + q.
+template <class R>
+struct SepReg2Args {
+    int lc, rk;
+    int q, lq;                   // tile width Q = 2^lq along the inner index; blockDim = N Q
+    int64_t outer, inner, nchunks;
+    const cx<R> *in;
+    cx<R> *out;
+    const cx<R> *coef_a, *coef_b;
+    const float4 *cf4_a, *cf4_b;   // complex64 paired-FMA coefficients (see SepRegArgs)
+    int ld_a[SEPR_MAXN], st_a[SEPR_MAXN];   // grid positions of mode ka's level-0 entries
+    int ld_b[SEPR_MAXN], st_b[SEPR_MAXN];   // and of mode kb's
+};
+
+template <class R>
+cudaError_t launch_sep_reg2(bool adjoint, const SepReg2Args<R> &a, cudaStream_t st);
 template <class R>
 bool sep_reg_supported(int lc, int rk);
 

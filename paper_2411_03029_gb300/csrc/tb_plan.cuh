@@ -120,6 +120,7 @@ struct tb_plan {
     int sepr_rk[TB_MAX_D] = {0};
     tb::c128 *sepr_coef64[TB_MAX_D] = {nullptr};
     tb::c64 *sepr_coef32[TB_MAX_D] = {nullptr};
+    float4 *sepr_cf4[2][TB_MAX_D] = {{nullptr}};   // paired-FMA form: [0] forward, [1] adjoint
     int sepr_ld[TB_MAX_D][tb::SEPR_MAXN] = {{0}};
     int sepr_st[TB_MAX_D][tb::SEPR_MAXN] = {{0}};
 

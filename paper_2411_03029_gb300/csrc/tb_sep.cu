@@ -167,6 +167,10 @@ template cudaError_t launch_sep_fiber<double>(const SepFiberArgs<double> &, cuda
 // stride, and when N <= 16 the next fiber's loads are issued before the
 // current fiber's arithmetic.
 constexpr int SEPR_THREADS = 128;
+// padding (complex entries) between the rows of a fused pair's shared tile:
+// phase 1 writes runs of Q entries from N Q apart, and the pad spreads them
+// over both halves of the banks
+constexpr int SEPR2_PAD = 8;
 
 // Complex coefficients from shared memory.  The asm is volatile so that the
 // loads stay inside the fiber loop: hoisting the loop-invariant coefficients
@@ -288,9 +292,146 @@ TB_HD void sepr_chain(const cx<R> *__restrict__ cs, cx<R> (&x)[RK << (2 * LC)]) 
     }
 }
 
-template <class R, int LC, int RK, bool ADJ>
-__global__ void __launch_bounds__(SEPR_THREADS, (RK << (2 * LC)) * sizeof(R) <= 64 ? 3 : 2)
-    k_sep_reg(const SepRegArgs<R> a) {
+// ---- complex64 with paired FP32 FMAs (fma.rn.f32x2, two lanes per
+// instruction).  Coefficients are float4 (re, re, im, im) forward and
+// (re, re, im, -im) adjoint, one 16-byte shared load each, feeding F fibers.
+// Forward (gather): A = sum (re, re) * x, B = sum (im, im) * x over a row, then
+// y = (A.x - B.y, A.y + B.x).  Adjoint (scatter):
+// y[col] += (re, re) * x + (im, -im) * (x.y, x.x) = conj(c) x.
+TB_HD float4 seprf_lds(const float4 *p) {
+#ifdef __CUDA_ARCH__
+    const unsigned s = (unsigned)__cvta_generic_to_shared(p);
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(s));
+    return v;
+#else
+    return *p;
+#endif
+}
+TB_HD float2 seprf_fma2(float2 a, float2 b, float2 c) {
+#ifdef __CUDA_ARCH__
+    return __ffma2_rn(a, b, c);
+#else
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+
+template <int LC, int RK, bool ADJ, int F, int ST>
+TB_HD void seprf_step(const float4 *__restrict__ cs, const float2 (&x)[F][RK << (2 * LC)],
+                      float2 (&y)[F][RK << (2 * LC)]) {
+    constexpr int N = RK << (2 * LC);
+    constexpr int K = sepr_width(LC, RK, ST);
+    const float4 *c = cs + sepr_off(LC, RK, ST);
+    if constexpr (!ADJ) {
+#pragma unroll
+        for (int e = 0; e < N; ++e) {
+            float2 A[F], B[F];
+#pragma unroll
+            for (int f = 0; f < F; ++f) A[f] = B[f] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const float4 cc = seprf_lds(c + e * K + j);
+                const float2 cr = make_float2(cc.x, cc.y), ci = make_float2(cc.z, cc.w);
+                const int col = sepr_col(LC, RK, ST, e, j);
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    A[f] = seprf_fma2(cr, x[f][col], A[f]);
+                    B[f] = seprf_fma2(ci, x[f][col], B[f]);
+                }
+            }
+#pragma unroll
+            for (int f = 0; f < F; ++f) y[f][e] = make_float2(A[f].x - B[f].y, A[f].y + B[f].x);
+        }
+    } else {
+#pragma unroll
+        for (int f = 0; f < F; ++f)
+#pragma unroll
+            for (int e = 0; e < N; ++e) y[f][e] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int e = 0; e < N; ++e) {
+            float2 xs[F];
+#pragma unroll
+            for (int f = 0; f < F; ++f) xs[f] = make_float2(x[f][e].y, x[f][e].x);
+#pragma unroll
+            for (int j = 0; j < K; ++j) {
+                const float4 cc = seprf_lds(c + e * K + j);
+                const float2 cr = make_float2(cc.x, cc.y), ci = make_float2(cc.z, cc.w);
+                const int col = sepr_col(LC, RK, ST, e, j);
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    y[f][col] = seprf_fma2(cr, x[f][e], y[f][col]);
+                    y[f][col] = seprf_fma2(ci, xs[f], y[f][col]);
+                }
+            }
+        }
+    }
+}
+
+// steps I .. 2 Lc of the chain (forward order; the adjoint runs them
+// reversed), ping-ponging between the two register arrays; the step index is
+// a template argument so every register index is a compile-time constant
+template <int LC, int RK, bool ADJ, int F, int I>
+TB_HD void seprf_chain_from(const float4 *__restrict__ cs, float2 (&x)[F][RK << (2 * LC)],
+                            float2 (&y)[F][RK << (2 * LC)]) {
+    if constexpr (I <= 2 * LC) {
+        seprf_step<LC, RK, ADJ, F, ADJ ? 2 * LC - I : I>(cs, x, y);
+        seprf_chain_from<LC, RK, ADJ, F, I + 1>(cs, y, x);
+    }
+}
+
+template <int LC, int RK, bool ADJ, int F>
+TB_HD void seprf_chain(const float4 *__restrict__ cs, float2 (&x)[F][RK << (2 * LC)]) {
+    constexpr int N = RK << (2 * LC);
+    float2 y[F][N];
+    seprf_chain_from<LC, RK, ADJ, F, 0>(cs, x, y);
+    // 2 Lc + 1 steps: the result is in y
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int e = 0; e < N; ++e) x[f][e] = y[f][e];
+}
+
+// Per-mode register chain, complex64 paired-FMA form: each thread takes F
+// fibers (f, f + T, ..., consecutive threads on consecutive fibers) and
+// issues all F N loads before it stages the block's coefficients, so the
+// loads are in flight during the staging.  One batch per thread (no
+// grid-stride loop): the load / store offsets, kernel parameters, are then
+// read where they are used instead of being held in registers.
+template <int LC, int RK, bool ADJ, int F, int MINB>
+__global__ void __launch_bounds__(SEPR_THREADS, MINB) k_sep_regf(const SepRegArgs<float> a) {
+    constexpr int N = RK << (2 * LC);
+    constexpr int NC = sepr_ncoef(LC, RK);
+    __shared__ __align__(16) float4 cs[NC];
+    const int *ldo = ADJ ? a.sto : a.ldo;
+    const int *sto = ADJ ? a.ldo : a.sto;
+    const int64_t total = a.outer * a.inner, inner = a.inner;
+    const int64_t f0 = (int64_t)blockIdx.x * blockDim.x * F + threadIdx.x;
+    const float2 *in = reinterpret_cast<const float2 *>(a.in);
+    float2 *out = reinterpret_cast<float2 *>(a.out);
+    float2 x[F][N];
+    int64_t base[F];
+#pragma unroll
+    for (int f = 0; f < F; ++f) {
+        const int64_t fi = f0 + (int64_t)f * blockDim.x;
+        const int64_t o = fi / inner;
+        base[f] = fi < total ? o * N * inner + (fi - o * inner) : -1;
+    }
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int p = 0; p < N; ++p) x[f][p] = base[f] >= 0 ? in[base[f] + ldo[p]] : make_float2(0.f, 0.f);
+    for (int i = threadIdx.x; i < NC; i += blockDim.x) cs[i] = a.cf4[i];
+    __syncthreads();
+    seprf_chain<LC, RK, ADJ, F>(cs, x);
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+        if (base[f] >= 0)
+#pragma unroll
+            for (int p = 0; p < N; ++p) out[base[f] + sto[p]] = x[f][p];
+}
+
+template <class R, int LC, int RK, bool ADJ, int MINB>
+__global__ void __launch_bounds__(SEPR_THREADS, MINB) k_sep_reg(const SepRegArgs<R> a) {
     constexpr int N = RK << (2 * LC);
     constexpr int NC = sepr_ncoef(LC, RK);
     constexpr bool PF = N * sizeof(R) <= 64;
@@ -330,15 +471,146 @@ __global__ void __launch_bounds__(SEPR_THREADS, (RK << (2 * LC)) * sizeof(R) <= 
     }
 }
 
-template <class R, int LC, int RK>
+// Fused pair of modes (SepReg2Args): phase 1 applies mode kb to the fibers
+// (o, i_ka = r, q) read from global memory and writes them to the shared tile
+// in grid order; phase 2 applies mode ka to the fibers (o, i_kb = r, q) read
+// from the tile and writes global memory.  Thread t = (r, qi) in both phases;
+// the tile is (i_ka N + i_kb) Q + qi, so each warp's shared accesses are runs
+// of Q consecutive entries.  Threads past the end of the inner range compute
+// on zeros and store nothing.
+template <class R, int LC, int RK, bool ADJ>
+TB_HD void sepr2_phase1(const SepReg2Args<R> &a, const cx<R> *csb, cx<R> *tile, int64_t blk, int t) {
+    constexpr int N = RK << (2 * LC);
+    const int lq = a.lq, qi = t & ((1 << lq) - 1), r = t >> lq;
+    const int64_t o = blk / a.nchunks, inner = a.inner;
+    const int64_t q = ((blk - o * a.nchunks) << lq) + qi;
+    const bool valid = q < inner;
+    const int *ldb = ADJ ? a.st_b : a.ld_b, *stb = ADJ ? a.ld_b : a.st_b;
+    cx<R> x[N];
+    const cx<R> *src = a.in + ((o * N + r) * N) * inner + q;
+#pragma unroll
+    for (int p = 0; p < N; ++p) x[p] = valid ? src[(int64_t)ldb[p] * inner] : cx<R>{R(0), R(0)};
+    sepr_chain<R, LC, RK, ADJ>(csb, x);
+#pragma unroll
+    for (int p = 0; p < N; ++p) tile[((r * N + stb[p]) << lq) + qi] = x[p];
+}
+
+template <class R, int LC, int RK, bool ADJ>
+TB_HD void sepr2_phase2(const SepReg2Args<R> &a, const cx<R> *csa, const cx<R> *tile, int64_t blk, int t) {
+    constexpr int N = RK << (2 * LC);
+    const int lq = a.lq, qi = t & ((1 << lq) - 1), r = t >> lq;
+    const int64_t o = blk / a.nchunks, inner = a.inner;
+    const int64_t q = ((blk - o * a.nchunks) << lq) + qi;
+    const int *lda = ADJ ? a.st_a : a.ld_a, *sta = ADJ ? a.ld_a : a.st_a;
+    cx<R> x[N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) x[p] = tile[((lda[p] * N + r) << lq) + qi];
+    sepr_chain<R, LC, RK, ADJ>(csa, x);
+    if (q < inner) {
+        cx<R> *dst = a.out + (o * N * N + r) * inner + q;
+#pragma unroll
+        for (int p = 0; p < N; ++p) dst[(int64_t)sta[p] * N * inner] = x[p];
+    }
+}
+
+// complex64 phases of the fused pair with the paired-FMA chain
+template <int LC, int RK, bool ADJ>
+TB_HD void seprf2_phase1(const SepReg2Args<float> &a, const float4 *csb, float2 *tile, int64_t blk, int t) {
+    constexpr int N = RK << (2 * LC);
+    const int lq = a.lq, qi = t & ((1 << lq) - 1), r = t >> lq;
+    const int64_t o = blk / a.nchunks, inner = a.inner;
+    const int64_t q = ((blk - o * a.nchunks) << lq) + qi;
+    const bool valid = q < inner;
+    const int *ldb = ADJ ? a.st_b : a.ld_b, *stb = ADJ ? a.ld_b : a.st_b;
+    float2 x[1][N];
+    const float2 *src = reinterpret_cast<const float2 *>(a.in) + ((o * N + r) * N) * inner + q;
+#pragma unroll
+    for (int p = 0; p < N; ++p) x[0][p] = valid ? src[(int64_t)ldb[p] * inner] : make_float2(0.f, 0.f);
+    seprf_chain<LC, RK, ADJ, 1>(csb, x);
+    const int pitch = (N << lq) + SEPR2_PAD;
+#pragma unroll
+    for (int p = 0; p < N; ++p) tile[r * pitch + (stb[p] << lq) + qi] = x[0][p];
+}
+
+template <int LC, int RK, bool ADJ>
+TB_HD void seprf2_phase2(const SepReg2Args<float> &a, const float4 *csa, const float2 *tile, int64_t blk, int t) {
+    constexpr int N = RK << (2 * LC);
+    const int lq = a.lq, qi = t & ((1 << lq) - 1), r = t >> lq;
+    const int64_t o = blk / a.nchunks, inner = a.inner;
+    const int64_t q = ((blk - o * a.nchunks) << lq) + qi;
+    const int *lda = ADJ ? a.st_a : a.ld_a, *sta = ADJ ? a.ld_a : a.st_a;
+    const int pitch = (N << lq) + SEPR2_PAD;
+    float2 x[1][N];
+#pragma unroll
+    for (int p = 0; p < N; ++p) x[0][p] = tile[lda[p] * pitch + (r << lq) + qi];
+    seprf_chain<LC, RK, ADJ, 1>(csa, x);
+    if (q < inner) {
+        float2 *dst = reinterpret_cast<float2 *>(a.out) + (o * N * N + r) * inner + q;
+#pragma unroll
+        for (int p = 0; p < N; ++p) dst[(int64_t)sta[p] * N * inner] = x[0][p];
+    }
+}
+
+template <int LC, int RK, bool ADJ>
+__global__ void __launch_bounds__(SEPR_THREADS, 4) k_sep_reg2f(const SepReg2Args<float> a) {
+    constexpr int NC = sepr_ncoef(LC, RK);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float4 *csb = reinterpret_cast<float4 *>(smraw);
+    float4 *csa = csb + NC;
+    float2 *tile = reinterpret_cast<float2 *>(csa + NC);
+    for (int i = threadIdx.x; i < NC; i += blockDim.x) {
+        csb[i] = a.cf4_b[i];
+        csa[i] = a.cf4_a[i];
+    }
+    __syncthreads();
+    seprf2_phase1<LC, RK, ADJ>(a, csb, tile, blockIdx.x, threadIdx.x);
+    __syncthreads();
+    seprf2_phase2<LC, RK, ADJ>(a, csa, tile, blockIdx.x, threadIdx.x);
+}
+
+template <class R, int LC, int RK, bool ADJ>
+__global__ void __launch_bounds__(SEPR_THREADS, 4) k_sep_reg2(const SepReg2Args<R> a) {
+    constexpr int NC = sepr_ncoef(LC, RK);
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<R> *csb = reinterpret_cast<cx<R> *>(smraw);
+    cx<R> *csa = csb + NC;
+    cx<R> *tile = csa + NC;
+    for (int i = threadIdx.x; i < NC; i += blockDim.x) {
+        csb[i] = a.coef_b[i];
+        csa[i] = a.coef_a[i];
+    }
+    __syncthreads();
+    sepr2_phase1<R, LC, RK, ADJ>(a, csb, tile, blockIdx.x, threadIdx.x);
+    __syncthreads();
+    sepr2_phase2<R, LC, RK, ADJ>(a, csa, tile, blockIdx.x, threadIdx.x);
+}
+
+template <class R, int LC, int RK, int MINB>
 static cudaError_t launch_sep_reg_t(bool adjoint, const SepRegArgs<R> &a, cudaStream_t st) {
-    void (*fn)(const SepRegArgs<R>) = adjoint ? k_sep_reg<R, LC, RK, true> : k_sep_reg<R, LC, RK, false>;
+    void (*fn)(const SepRegArgs<R>) =
+        adjoint ? k_sep_reg<R, LC, RK, true, MINB> : k_sep_reg<R, LC, RK, false, MINB>;
     const int64_t total = a.outer * a.inner;
     if (total <= 0) return cudaSuccess;
     int64_t blocks = (total + SEPR_THREADS - 1) / SEPR_THREADS;
     if (a.blocks > 0 && a.blocks < blocks) blocks = a.blocks;
     if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
     fn<<<(unsigned)blocks, SEPR_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <class R, int LC, int RK>
+static cudaError_t launch_sep_reg2_t(bool adjoint, const SepReg2Args<R> &a, cudaStream_t st) {
+    void (*fn)(const SepReg2Args<R>) = adjoint ? k_sep_reg2<R, LC, RK, true> : k_sep_reg2<R, LC, RK, false>;
+    constexpr int N = RK << (2 * LC);
+    const int threads = N << a.lq;
+    if (threads > SEPR_THREADS || threads < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)(2 * sepr_ncoef(LC, RK) + N * N * (1 << a.lq)) * sizeof(cx<R>);
+    cudaError_t e = set_smem_once((const void *)fn, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = a.outer * a.nchunks;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    fn<<<(unsigned)blocks, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -350,31 +622,104 @@ bool sep_reg_supported(int lc, int rk) {
 }
 
 template <class R>
-cudaError_t launch_sep_reg(bool adjoint, const SepRegArgs<R> &a, cudaStream_t st) {
+cudaError_t launch_sep_reg(bool adjoint, int variant, const SepRegArgs<R> &a, cudaStream_t st) {
     if (!sep_reg_supported<R>(a.lc, a.rk)) return cudaErrorInvalidValue;
     switch (a.rk) {
-        case 1: return launch_sep_reg_t<R, 1, 1>(adjoint, a, st);
-        case 2: return launch_sep_reg_t<R, 1, 2>(adjoint, a, st);
+        case 1: return launch_sep_reg_t<R, 1, 1, 3>(adjoint, a, st);
+        case 2: return launch_sep_reg_t<R, 1, 2, 3>(adjoint, a, st);
         default: break;
     }
+    (void)variant;
     return cudaErrorInvalidValue;
 }
 
-// the longer fibers are instantiated for complex64 only
+template <class R>
+cudaError_t launch_sep_reg2(bool adjoint, const SepReg2Args<R> &a, cudaStream_t st) {
+    if (!sep_reg_supported<R>(a.lc, a.rk)) return cudaErrorInvalidValue;
+    switch (a.rk) {
+        case 1: return launch_sep_reg2_t<R, 1, 1>(adjoint, a, st);
+        case 2: return launch_sep_reg2_t<R, 1, 2>(adjoint, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int LC, int RK, int F, int MINB>
+static cudaError_t launch_sep_regf_t(bool adjoint, const SepRegArgs<float> &a, cudaStream_t st) {
+    void (*fn)(const SepRegArgs<float>) =
+        adjoint ? k_sep_regf<LC, RK, true, F, MINB> : k_sep_regf<LC, RK, false, F, MINB>;
+    const int64_t total = a.outer * a.inner;
+    if (total <= 0) return cudaSuccess;
+    const int64_t blocks = (total + (int64_t)SEPR_THREADS * F - 1) / ((int64_t)SEPR_THREADS * F);
+    if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    fn<<<(unsigned)blocks, SEPR_THREADS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int LC, int RK>
+static cudaError_t launch_sep_reg2f_t(bool adjoint, const SepReg2Args<float> &a, cudaStream_t st) {
+    void (*fn)(const SepReg2Args<float>) = adjoint ? k_sep_reg2f<LC, RK, true> : k_sep_reg2f<LC, RK, false>;
+    constexpr int N = RK << (2 * LC);
+    const int threads = N << a.lq;
+    if (threads > SEPR_THREADS || threads < 1) return cudaErrorInvalidValue;
+    const size_t smem = (size_t)2 * sepr_ncoef(LC, RK) * sizeof(float4) +
+                        (size_t)N * ((N << a.lq) + SEPR2_PAD) * sizeof(float2);
+    cudaError_t e = set_smem_once((const void *)fn, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = a.outer * a.nchunks;
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
+    fn<<<(unsigned)blocks, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+// complex64: the paired-FMA form with two fibers per thread up to N = 16
+// (variant 0, 3 resident blocks per SM) or one (variant 2, 4 blocks), and
+// the scalar form with prefetch (variant 1), for rk up to 8
 template <>
-cudaError_t launch_sep_reg<float>(bool adjoint, const SepRegArgs<float> &a, cudaStream_t st) {
+cudaError_t launch_sep_reg<float>(bool adjoint, int variant, const SepRegArgs<float> &a, cudaStream_t st) {
+    if (!sep_reg_supported<float>(a.lc, a.rk)) return cudaErrorInvalidValue;
+    if (variant == 0) {
+        switch (a.rk) {
+            case 1: return launch_sep_regf_t<1, 1, 2, 3>(adjoint, a, st);
+            case 2: return launch_sep_regf_t<1, 2, 2, 3>(adjoint, a, st);
+            case 4: return launch_sep_regf_t<1, 4, 2, 3>(adjoint, a, st);
+            case 8: return launch_sep_regf_t<1, 8, 1, 3>(adjoint, a, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (variant == 2) {
+        switch (a.rk) {
+            case 1: return launch_sep_regf_t<1, 1, 1, 4>(adjoint, a, st);
+            case 2: return launch_sep_regf_t<1, 2, 1, 4>(adjoint, a, st);
+            case 4: return launch_sep_regf_t<1, 4, 1, 4>(adjoint, a, st);
+            case 8: return launch_sep_regf_t<1, 8, 1, 3>(adjoint, a, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    switch (a.rk) {
+        case 1: return launch_sep_reg_t<float, 1, 1, 3>(adjoint, a, st);
+        case 2: return launch_sep_reg_t<float, 1, 2, 3>(adjoint, a, st);
+        case 4: return launch_sep_reg_t<float, 1, 4, 3>(adjoint, a, st);
+        case 8: return launch_sep_reg_t<float, 1, 8, 2>(adjoint, a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <>
+cudaError_t launch_sep_reg2<float>(bool adjoint, const SepReg2Args<float> &a, cudaStream_t st) {
     if (!sep_reg_supported<float>(a.lc, a.rk)) return cudaErrorInvalidValue;
     switch (a.rk) {
-        case 1: return launch_sep_reg_t<float, 1, 1>(adjoint, a, st);
-        case 2: return launch_sep_reg_t<float, 1, 2>(adjoint, a, st);
-        case 4: return launch_sep_reg_t<float, 1, 4>(adjoint, a, st);
-        case 8: return launch_sep_reg_t<float, 1, 8>(adjoint, a, st);
+        case 1: return launch_sep_reg2f_t<1, 1>(adjoint, a, st);
+        case 2: return launch_sep_reg2f_t<1, 2>(adjoint, a, st);
+        case 4: return launch_sep_reg2f_t<1, 4>(adjoint, a, st);
+        case 8: return launch_sep_reg2f_t<1, 8>(adjoint, a, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template bool sep_reg_supported<float>(int, int);
 template bool sep_reg_supported<double>(int, int);
-template cudaError_t launch_sep_reg<double>(bool, const SepRegArgs<double> &, cudaStream_t);
+template cudaError_t launch_sep_reg<double>(bool, int, const SepRegArgs<double> &, cudaStream_t);
+template cudaError_t launch_sep_reg2<double>(bool, const SepReg2Args<double> &, cudaStream_t);
 
 }  // namespace tb

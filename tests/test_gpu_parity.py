@@ -264,14 +264,16 @@ def test_config_radon2d_n256_sampled():
                                           (2, 32, 4, (tb.PREC_C64,)), (6, 4, 5, (tb.PREC_C64, tb.PREC_C128))])
 def test_separable_register_chains_match_shared_memory_fibers(d, n, nv, precs):
     """With ranks equal to the leaf size (bit-reversed uniform Fourier, L = 2) the
-    register-resident chains apply the same steps as the shared-memory fiber
-    passes: both agree to rounding, and with the DFT identity."""
+    register-resident chains (per mode with paired or scalar FMAs and one or
+    two fibers per thread, and fused in pairs of modes) apply the same steps as the shared-memory fiber
+    passes: all agree to rounding, and with the DFT identity."""
     w = W.Workload(name="f", kind=W.FOURIER, d=d, n=n, tol=1e-8, nv=nv, precision=W.C64, bound=1e-5,
                    rhs_seeds=tuple(range(nv)), samples=0, order=W.ORDER_BITREV, L=2)
     f = W.rhs(w)
     ref = oracle.fourier_fft(f.numpy(), d).reshape(-1, nv)
     refv = oracle.workload_apply_adjoint(w, f)
-    ops = {s: tb.from_workload(w, sep_schedule=s) for s in (tb.SEP_FIBER, tb.SEP_REGISTER)}
+    schedules = (tb.SEP_FIBER, tb.SEP_REGISTER, tb.SEP_REGISTER_PAIRS, tb.SEP_REGISTER_SCALAR, tb.SEP_REGISTER_ONE)
+    ops = {s: tb.from_workload(w, sep_schedule=s) for s in schedules}
     for prec in precs:
         out = {}
         for s, op in ops.items():
@@ -279,13 +281,15 @@ def test_separable_register_chains_match_shared_memory_fibers(d, n, nv, precs):
             out[s] = (run(op, w, f, prec), run(op, w, f, prec, adjoint=True))
             names = {r["name"] for r in op.profile_stats()}
             op.profile(False)
-            assert ("sep_reg" in names) == (s == tb.SEP_REGISTER), names
+            assert ("sep_reg" in names) == (s in (tb.SEP_REGISTER, tb.SEP_REGISTER_SCALAR, tb.SEP_REGISTER_ONE)
+                                            or (s == tb.SEP_REGISTER_PAIRS and d % 2 == 1)), names
+            assert ("sep_reg2" in names) == (s == tb.SEP_REGISTER_PAIRS), names
         tight = 1e-12 if prec == tb.PREC_C128 else 2e-6
         for s in out:
-            assert rel(out[s][0], ref) < tight
-            assert rel(out[s][1], refv) < tight
-        assert rel(out[tb.SEP_REGISTER][0], out[tb.SEP_FIBER][0]) < tight
-        assert rel(out[tb.SEP_REGISTER][1], out[tb.SEP_FIBER][1]) < tight
+            assert rel(out[s][0], ref) < tight, s
+            assert rel(out[s][1], refv) < tight, s
+            assert rel(out[s][0], out[tb.SEP_FIBER][0]) < tight, s
+            assert rel(out[s][1], out[tb.SEP_FIBER][1]) < tight, s
     for op in ops.values():
         op.close()
 
