@@ -154,6 +154,8 @@ class ClockSampler:
 # precision and pass; see profiles/ for the command.  Entries are removed when
 # the kernel changes.
 TRAFFIC = {("helmholtz3d_n256", 2, "core@l2"): 6.00e9 + 645.72e6}
+# every per-mode register pass of fourier6d_n16 reads and writes the whole tensor once
+TRAFFIC.update({("fourier6d_n16", 1, f"sep_reg@l{k}"): 1.073863e9 + 1.025651e9 for k in range(6)})
 
 
 def level_mode_bytes(info, w, nv, es):
