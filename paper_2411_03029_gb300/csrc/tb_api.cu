@@ -1395,7 +1395,7 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
                         a.ldo[p] = (int)(h->sepr_ld[k][p] * a.inner);
                         a.sto[p] = (int)(h->sepr_st[k][p] * a.inner);
                     }
-                    a.blocks = g_num_sms * 3;
+                    a.blocks = (int)g_num_sms * 3;   // grid of the persistent scalar form
                     ProfRec r{"sep_reg", k, (int)adjoint, nullptr, nullptr, 0, 0.0};
                     if (prof) {
                         r.bytes = 2 * N * nv * es + h->sep_nnz[dir][k] * (es + 4);
@@ -1404,7 +1404,8 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
                         TB_CK(cudaEventCreate(&r.e1));
                         TB_CK(cudaEventRecord(r.e0, st));
                     }
-                    TB_CK(launch_sep_reg<R>(adjoint, h->sep_choice == 5 ? 1 : h->sep_choice == 6 ? 2 : 0, a, st));
+                    const int variant = h->sep_choice == 5 ? 1 : h->sep_choice == 6 ? 2 : 0;
+                    TB_CK(launch_sep_reg<R>(adjoint, variant, a, st));
                     if (prof) {
                         TB_CK(cudaEventRecord(r.e1, st));
                         h->prof.push_back(r);

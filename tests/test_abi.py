@@ -56,7 +56,7 @@ def test_build_rejects_an_unknown_separable_schedule_without_touching_the_gpu(li
         grids.y[k] = ys[k].ctypes.data
     opt = tb._Options()
     assert lib.tb_options_default(ctypes.byref(opt)) == 0
-    opt.sep_schedule = 7
+    opt.sep_schedule = 99
     n = (ctypes.c_int64 * 2)(16, 16)
     h = ctypes.c_void_p()
     assert lib.tb_build_ex(ctypes.byref(kern), 2, ctypes.cast(n, ctypes.c_void_p), ctypes.byref(grids), 1e-6,
