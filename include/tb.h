@@ -194,6 +194,22 @@ tb_status tb_apply_adjoint(tb_handle h, const void *g, void *v, int64_t nv, int 
 tb_status tb_apply_host(tb_handle h, const void *f, void *u, int64_t nv, int precision);
 
 /*
+ * u_i = K f_i for count inputs with HOST buffers, pipelined: the copy of input
+ * i + 1 to the device and the copy of result i - 1 to the host run while input
+ * i is applied, on three streams owned by the handle (host-to-device, apply,
+ * device-to-host) with two device buffer pairs.  Every input is copied in and
+ * every result copied out inside the call; it returns when all results are in
+ * host memory (synchronous).  f[i] and u[i] are host pointers of the tb_apply
+ * layout, all of the same nv; the copies overlap only when they are pinned
+ * (page-locked) memory.  The paper has no counterpart: this is the library's
+ * host-data path.
+ * Errors: TB_EINVAL for NULL arrays or pointers, count < 1 or nv < 1; as
+ * tb_apply otherwise (on an error the streams are synchronized before return).
+ */
+tb_status tb_apply_host_batch(tb_handle h, const void *const *f, void *const *u, int64_t count, int64_t nv,
+                              int precision);
+
+/*
  * u = K f without allocating any device memory.  (The paper has no
  * counterpart: this is an interface of this library.)
  *

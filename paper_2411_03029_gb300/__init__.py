@@ -32,7 +32,7 @@ STATUS = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "TB_ERAN
 # every symbol declared in include/tb.h
 EXPORTS = ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
            "tb_apply_host", "tb_query", "tb_free", "tb_last_error", "tb_version",
-           "tb_profile_enable", "tb_profile_stats", "tb_apply_noalloc", "tb_autotune")
+           "tb_profile_enable", "tb_profile_stats", "tb_apply_noalloc", "tb_autotune", "tb_apply_host_batch")
 
 
 class TBError(RuntimeError):
@@ -107,9 +107,10 @@ def lib():
         L.tb_profile_enable.argtypes = [P, ctypes.c_int]
         L.tb_profile_stats.argtypes = [P, ctypes.POINTER(_PassStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.tb_apply_noalloc.argtypes = [P, P, P, I64, ctypes.c_int, P]
+        L.tb_apply_host_batch.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), I64, I64, ctypes.c_int]
         for name in ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
                      "tb_apply_host", "tb_query", "tb_free", "tb_profile_enable", "tb_profile_stats",
-                     "tb_apply_noalloc"):
+                     "tb_apply_noalloc", "tb_apply_host_batch"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -250,6 +251,23 @@ class TBOperator:
     def apply_adjoint(self, g, precision: int | None = None, out=None):
         """v = K^H g on the current torch stream (tb_apply_adjoint)."""
         return self._run(lib().tb_apply_adjoint, g, precision, out)
+
+    def apply_host_batch(self, fs, us, precision: int | None = None):
+        """u_i = K f_i for lists of host arrays (numpy, pinned for overlap), with the
+        copies of neighbouring inputs and results overlapping the applies
+        (tb_apply_host_batch).  Results are written into `us`."""
+        precision = self.precision if precision is None else precision
+        dt = np.complex128 if precision == PREC_C128 else np.complex64
+        if len(fs) != len(us) or not fs:
+            raise ValueError("fs and us must be non-empty lists of the same length")
+        for a in list(fs) + list(us):
+            if a.dtype != dt or not a.flags.c_contiguous:
+                raise TypeError(f"host arrays must be C-contiguous {dt}")
+        nv = fs[0].shape[-1] if fs[0].ndim == self.d + 1 else 1
+        fp = (ctypes.c_void_p * len(fs))(*[a.ctypes.data for a in fs])
+        up = (ctypes.c_void_p * len(us))(*[a.ctypes.data for a in us])
+        _check(lib().tb_apply_host_batch(self._h, fp, up, len(fs), nv, precision))
+        return us
 
     def apply_host(self, f: np.ndarray, precision: int | None = None) -> np.ndarray:
         """u = K f with host arrays; copies in and out inside the call (tb_apply_host)."""

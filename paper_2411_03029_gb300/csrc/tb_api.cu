@@ -133,6 +133,14 @@ tb_status tb_free(tb_handle h) {
     if (h->ws.mbuf[1]) cudaFree(h->ws.mbuf[1]);
     if (h->ws.host_in) cudaFree(h->ws.host_in);
     if (h->ws.host_out) cudaFree(h->ws.host_out);
+    for (int b = 0; b < 2; ++b) {
+        if (h->pipe.din[b]) cudaFree(h->pipe.din[b]);
+        if (h->pipe.dout[b]) cudaFree(h->pipe.dout[b]);
+        for (cudaEvent_t e : {h->pipe.in_ready[b], h->pipe.in_free[b], h->pipe.out_ready[b], h->pipe.out_free[b]})
+            if (e) cudaEventDestroy(e);
+    }
+    for (int i = 0; i < 3; ++i)
+        if (h->pipe.s[i]) cudaStreamDestroy(h->pipe.s[i]);
     cudaSetDevice(cur);
     delete h;
     return TB_OK;
@@ -1938,6 +1946,66 @@ extern "C" tb_status tb_apply_host(tb_handle h, const void *f, void *u, int64_t 
     TB_TRY(apply_common(h, h->ws.host_in, h->ws.host_out, nv, precision, nullptr, false));
     TB_CK(cudaMemcpy(u, h->ws.host_out, bytes, cudaMemcpyDeviceToHost));
     return TB_OK;
+}
+
+extern "C" tb_status tb_apply_host_batch(tb_handle h, const void *const *f, void *const *u, int64_t count,
+                                         int64_t nv, int precision) {
+    if (!h || !f || !u) return fail(TB_EINVAL, "handle, f and u must be non-NULL");
+    if (count < 1) return fail(TB_EINVAL, "count must be positive");
+    if (nv <= 0) return fail(TB_EINVAL, "nv must be positive");
+    for (int64_t i = 0; i < count; ++i)
+        if (!f[i] || !u[i]) return fail(TB_EINVAL, "f[i] and u[i] must be non-NULL");
+    int64_t N = 1;
+    for (int k = 0; k < h->d; ++k) N *= h->n[k];
+    const size_t bytes = (size_t)N * nv * (precision == TB_PREC_C128 ? 16 : 8);
+    if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
+    HostPipe &P = h->pipe;
+    if (!P.s[0]) {
+        for (int i = 0; i < 3; ++i) TB_CK(cudaStreamCreateWithFlags(&P.s[i], cudaStreamNonBlocking));
+        for (int b = 0; b < 2; ++b)
+            for (cudaEvent_t *e : {&P.in_ready[b], &P.in_free[b], &P.out_ready[b], &P.out_free[b]})
+                TB_CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    if (bytes > P.bytes) {
+        for (int i = 0; i < 3; ++i) TB_CK(cudaStreamSynchronize(P.s[i]));
+        for (int b = 0; b < 2; ++b) {
+            if (P.din[b]) cudaFree(P.din[b]);
+            if (P.dout[b]) cudaFree(P.dout[b]);
+            P.din[b] = P.dout[b] = nullptr;
+        }
+        P.bytes = 0;
+        for (int b = 0; b < 2; ++b) {
+            TB_CK(cudaMalloc(&P.din[b], bytes));
+            TB_CK(cudaMalloc(&P.dout[b], bytes));
+        }
+        P.bytes = bytes;
+    }
+    auto body = [&]() -> tb_status {
+        for (int64_t i = 0; i < count; ++i) {
+            const int b = (int)(i & 1);
+            // input i into din[b] once the apply of input i - 2 has read it
+            if (i >= 2) TB_CK(cudaStreamWaitEvent(P.s[0], P.in_free[b], 0));
+            TB_CK(cudaMemcpyAsync(P.din[b], f[i], bytes, cudaMemcpyHostToDevice, P.s[0]));
+            TB_CK(cudaEventRecord(P.in_ready[b], P.s[0]));
+            // apply once the input is there and result i - 2 has left dout[b]
+            TB_CK(cudaStreamWaitEvent(P.s[1], P.in_ready[b], 0));
+            if (i >= 2) TB_CK(cudaStreamWaitEvent(P.s[1], P.out_free[b], 0));
+            TB_TRY(apply_common(h, P.din[b], P.dout[b], nv, precision, P.s[1], false));
+            TB_CK(cudaEventRecord(P.in_free[b], P.s[1]));
+            TB_CK(cudaEventRecord(P.out_ready[b], P.s[1]));
+            // result i back to the host
+            TB_CK(cudaStreamWaitEvent(P.s[2], P.out_ready[b], 0));
+            TB_CK(cudaMemcpyAsync(u[i], P.dout[b], bytes, cudaMemcpyDeviceToHost, P.s[2]));
+            TB_CK(cudaEventRecord(P.out_free[b], P.s[2]));
+        }
+        return TB_OK;
+    };
+    const tb_status st = body();
+    for (int i = 0; i < 3; ++i) {
+        const cudaError_t e = cudaStreamSynchronize(P.s[i]);
+        if (e != cudaSuccess && st == TB_OK) return fail(TB_ECUDA, std::string("host batch: ") + cudaGetErrorString(e));
+    }
+    return st;
 }
 
 extern "C" tb_status tb_profile_enable(tb_handle h, int on) {

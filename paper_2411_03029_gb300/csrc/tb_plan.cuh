@@ -38,6 +38,17 @@ struct Workspace {
     size_t host_bytes = 0;
 };
 
+// Streams, events and device buffers of the pipelined host-data apply
+// (tb_apply_host_batch): [0] host-to-device, [1] apply, [2] device-to-host.
+struct HostPipe {
+    cudaStream_t s[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t in_ready[2] = {nullptr, nullptr}, in_free[2] = {nullptr, nullptr};
+    cudaEvent_t out_ready[2] = {nullptr, nullptr}, out_free[2] = {nullptr, nullptr};
+    void *din[2] = {nullptr, nullptr};
+    void *dout[2] = {nullptr, nullptr};
+    size_t bytes = 0;
+};
+
 struct ProfRec {
     const char *name;
     int level, adjoint;
@@ -132,6 +143,7 @@ struct tb_plan {
     int64_t level_max = 0;         // largest level tensor, entries per RHS
     int64_t mode_max[2] = {0, 0};  // largest even / odd mode intermediate, entries per RHS
     tb::Workspace ws;
+    tb::HostPipe pipe;
     std::vector<tb::GraphEntry> graphs;
     std::vector<void *> allocations;
     int64_t device_bytes = 0;

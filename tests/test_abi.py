@@ -92,6 +92,7 @@ def test_build_rejects_bad_arguments_without_touching_the_gpu(lib):
 
 
 def test_apply_rejects_null_handle(lib):
+    assert lib.tb_apply_host_batch(None, None, None, 1, 1, 1) == 1
     assert lib.tb_apply(None, None, None, 1, 0, None) == 1
     assert lib.tb_apply_adjoint(None, None, None, 1, 0, None) == 1
     assert lib.tb_query(None, None) == 1
