@@ -21,7 +21,7 @@ from . import build as _build
 TB_MAX_D = 6
 TB_MAX_LEVELS = 16
 
-KERNEL_FOURIER, KERNEL_HELMHOLTZ, KERNEL_RADON = 1, 2, 3
+KERNEL_FOURIER, KERNEL_HELMHOLTZ, KERNEL_RADON, KERNEL_RADON_ANISO = 1, 2, 3, 4
 PREC_C128, PREC_C64, PREC_C64_SPLITBF16 = 0, 1, 2
 SEP_RULE, SEP_FIBER, SEP_TILE, SEP_REGISTER, SEP_REGISTER_PAIRS, SEP_REGISTER_SCALAR, SEP_REGISTER_ONE = range(7)
 ORDER_AUTO, ORDER_NATURAL, ORDER_BITREV = -1, 0, 1

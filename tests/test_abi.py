@@ -105,3 +105,35 @@ def test_autotune_and_apply_reject_a_null_handle_without_touching_the_gpu(lib):
     opt = tb._Options()
     assert lib.tb_options_default(ctypes.byref(opt)) == 0
     assert opt.autotune == 0                                           # off unless asked for
+
+
+def test_build_rejects_bad_kernel_parameters_without_touching_the_gpu(lib):
+    import numpy as np
+    xs = [np.arange(16) / 16.0 for _ in range(3)]
+    ys = [np.arange(16) - 8.0 for _ in range(3)]
+    grids = tb._Grids()
+    for k in range(3):
+        grids.x[k] = xs[k].ctypes.data
+        grids.y[k] = ys[k].ctypes.data
+    n = (ctypes.c_int64 * 3)(16, 16, 16)
+    h = ctypes.c_void_p()
+    # the anisotropic Radon phase (Eq. randon2d) is defined for d = 2 only
+    aniso = tb._Kernel(tb.KERNEL_RADON_ANISO, (ctypes.c_double * 4)(2 / 16, 1 / 16, 2 / 16, 1 / 16))
+    assert lib.tb_build(ctypes.byref(aniso), 3, ctypes.cast(n, ctypes.c_void_p), ctypes.byref(grids), 1e-6,
+                        ctypes.byref(h)) == 1
+    assert b"d = 2" in lib.tb_last_error()
+    # a negative plate distance h
+    plates = tb._Kernel(tb.KERNEL_HELMHOLTZ, (ctypes.c_double * 4)(10.0, -1.0, 0.0, 0.0))
+    assert lib.tb_build(ctypes.byref(plates), 2, ctypes.cast(n, ctypes.c_void_p), ctypes.byref(grids), 1e-6,
+                        ctypes.byref(h)) == 1
+    assert b"offset" in lib.tb_last_error()
+    # h = 0 on coincident grids: the Green's function is singular
+    same = tb._Kernel(tb.KERNEL_HELMHOLTZ, (ctypes.c_double * 4)(10.0, 0.0, 0.0, 0.0))
+    g2 = tb._Grids()
+    for k in range(2):
+        g2.x[k] = xs[k].ctypes.data
+        g2.y[k] = xs[k].ctypes.data
+    assert lib.tb_build(ctypes.byref(same), 2, ctypes.cast(n, ctypes.c_void_p), ctypes.byref(g2), 1e-6,
+                        ctypes.byref(h)) == 1
+    assert b"coincides" in lib.tb_last_error()
+    assert not h.value
