@@ -5,9 +5,10 @@
 //    assembles from the factor blocks (source transfers W_l, Kronecker core,
 //    target transfers P_l) for Lc = 1..3 and ranks 1..8.
 // 2. The complex64 paired-FMA chains (seprf_chain, forward and adjoint, one or
-//    two fibers) and the fused pair phases (seprf2_phase1/2, padded tile) equal
-//    the dense product of their step matrices built from sepr_col, with the
-//    load / store positions as permutations.
+//    two fibers), the scalar chains (sepr_chain, complex64 and complex128) and
+//    the fused pair phases (seprf2_phase1/2, padded tile) equal the dense
+//    product of their step matrices built from sepr_col, with the load / store
+//    positions as permutations.
 #include <complex>
 #include <cstdio>
 #include <cstdlib>
@@ -143,6 +144,39 @@ static int check_chain() {
     return bad;
 }
 
+// the scalar chain (sepr_chain: complex128, and the complex64 prefetching form)
+template <class R, int RK>
+static int check_scalar_chain() {
+    constexpr int LC = 1, N = RK << 2, NC = sepr_ncoef(LC, RK);
+    std::vector<C> cd(NC);
+    for (auto &c : cd) c = C(rnd(), rnd());
+    std::vector<cx<R>> cs(NC);
+    for (int i = 0; i < NC; ++i) cs[i] = {(R)cd[i].real(), (R)cd[i].imag()};
+    int bad = 0;
+    for (int adj = 0; adj < 2; ++adj) {
+        cx<R> x[N];
+        std::vector<C> xr(N);
+        for (int p = 0; p < N; ++p) {
+            xr[p] = C(rnd(), rnd());
+            x[p] = {(R)xr[p].real(), (R)xr[p].imag()};
+        }
+        if (adj) sepr_chain<R, LC, RK, true>(cs.data(), x);
+        else sepr_chain<R, LC, RK, false>(cs.data(), x);
+        const std::vector<C> M = dense_chain<LC, RK>(cd, adj);
+        double num = 0, den = 0;
+        for (int r = 0; r < N; ++r) {
+            C acc = 0;
+            for (int c = 0; c < N; ++c) acc += M[r * N + c] * xr[c];
+            num += std::norm(C(x[r].x, x[r].y) - acc);
+            den += std::norm(acc);
+        }
+        const double err = std::sqrt(num / den);
+        printf("scalar chain rk %d bytes %zu adjoint %d: rel err %.2e\n", RK, sizeof(R), adj, err);
+        bad += err > (sizeof(R) == 4 ? 1e-5 : 1e-13);
+    }
+    return bad;
+}
+
 template <int RK>
 static int check_pair(int64_t outer, int64_t inner, bool adj) {
     constexpr int LC = 1, N = RK << 2, NC = sepr_ncoef(LC, RK);
@@ -231,6 +265,8 @@ int main() {
     srand(12345);
     int bad = check_pattern();
     bad += check_chain<1, 2>() + check_chain<2, 2>() + check_chain<4, 2>() + check_chain<4, 1>() + check_chain<8, 1>();
+    bad += check_scalar_chain<float, 1>() + check_scalar_chain<float, 2>() + check_scalar_chain<float, 4>() +
+           check_scalar_chain<float, 8>() + check_scalar_chain<double, 1>() + check_scalar_chain<double, 2>();
     for (int adj = 0; adj < 2; ++adj)
         bad += check_pair<1>(2, 3, adj) + check_pair<2>(3, 8, adj) + check_pair<4>(2, 8, adj) +
                check_pair<4>(1, 21, adj) + check_pair<8>(2, 5, adj) + check_pair<4>(3, 1, adj);
