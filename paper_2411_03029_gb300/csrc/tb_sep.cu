@@ -6,11 +6,18 @@
 // acts on one mode, so the tensor butterfly of Eq. (butterfly_tensor) is the
 // tensor product over modes of 1-D butterfly chains
 //     B_k = U_k P_k,1 .. P_k,Lc  K_k  W_k,Lc .. W_k,1 V_k ,
-// and u = f x_1 B_1 x_2 ... x_d B_d.  A thread block stages a tile that holds
-// complete fibers along a few consecutive modes (and a contiguous run of the
-// trailing modes and right-hand sides), and applies the step matrices of those
-// modes one after another in shared memory.  Each step is a small sparse
-// matrix (CSR) on the 1-D index of its mode.
+// and u = f x_1 B_1 x_2 ... x_d B_d.  Each step is a small sparse matrix (CSR)
+// on the 1-D index of its mode.  Three forms apply the chains:
+//   - k_sep_pass: a thread block stages a tile that holds complete fibers
+//     along a few consecutive modes (and a contiguous run of the trailing
+//     modes and right-hand sides) and applies those modes' steps one after
+//     another in shared memory;
+//   - k_sep_fiber: one pass per mode, each thread's fiber in a shared-memory
+//     column, the steps as packed nonzero streams;
+//   - k_sep_regf / k_sep_reg / k_sep_reg2: one pass per mode (or per pair of
+//     modes) with the fibers in registers, for modes whose ranks equal the
+//     leaf size, where every step is a compile-time pattern of dense blocks
+//     (sepr_col) and V, U^T fold into the load and store positions.
 #include "tb_kernels.cuh"
 
 namespace tb {
