@@ -48,7 +48,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the built-in launch shapes")
-    p.add_argument("--err-samples", type=int, default=16)
+    p.add_argument("--err-samples", type=int, default=4096,
+                   help="sampled outputs of the error check (the stored oracle values of the full-size "
+                        "3-D Helmholtz configuration when they apply; else the live oracle, capped)")
     p.add_argument("--profile-only", action="store_true", help="eager applies only (for ncu)")
     p.add_argument("--n", type=int, default=None, help="points per axis of a reduced-size copy (profiling)")
     p.add_argument("--sep-schedule", type=int, default=0,
@@ -153,7 +155,7 @@ class ClockSampler:
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload,
 # precision and pass; see profiles/ for the command.  Entries are removed when
 # the kernel changes.
-TRAFFIC = {("helmholtz3d_n256", 2, "core@l2"): 6.00e9 + 645.72e6}
+TRAFFIC = {}
 # every per-mode register pass of fourier6d_n16 reads and writes the whole tensor once
 TRAFFIC.update({("fourier6d_n16", 1, f"sep_reg@l{k}"): 1.073863e9 + 1.025651e9 for k in range(6)})
 
@@ -251,12 +253,49 @@ def reference_arm(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def rel_err_sampled(w, f_np, u_dev, count, seed=4096):
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+# direct-sum work the live error check may spend (kernel evaluations)
+LIVE_ORACLE_EVALS = 2.0e9
+
+
+def sampled_reference(w, f_np, count):
+    """Oracle values on sampled outputs: (rows, u_ref, cols, v_ref, source).
+
+    For the full-size 3-D Helmholtz configuration the values stored in
+    tests/golden/helmholtz3d_n256.npz (written by the script beside it, which
+    calls only oracle/) are used when the seeded inputs reproduce their
+    fingerprint; otherwise the direct sum runs here on `count` outputs, capped so
+    that it stays within a bounded number of kernel evaluations."""
+    path = os.path.join(GOLDEN, f"{w.name}.npz")
+    if os.path.exists(path):
+        z = np.load(path)
+        rows = z["rows"]
+        if np.array_equal(f_np.reshape(-1, w.nv)[rows[:16]], z["fingerprint"]):
+            k = min(count, len(rows))
+            return rows[:k], z["u"][:k], z["cols"][:k], z["v"][:k], "stored oracle values"
     import oracle
-    rows = W.sample_targets(w, count, seed=seed)
-    ref = oracle.workload_apply(w, f_np, rows)
-    u = u_dev.reshape(-1, w.nv)[torch.from_numpy(rows).cuda()].cpu().to(torch.complex128).numpy()
-    return float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+    count = int(max(16, min(count, LIVE_ORACLE_EVALS / w.N)))
+    rows = W.sample_targets(w, count, seed=4096)
+    cols = W.sample_targets(w, count, seed=4097)
+    return (rows, oracle.workload_apply(w, f_np, rows), cols, oracle.workload_apply_adjoint(w, f_np, cols),
+            "live oracle")
+
+
+def rel_err_rows(x_dev, nv, rows, ref):
+    x = x_dev.reshape(-1, nv)[torch.from_numpy(np.asarray(rows)).to(x_dev.device)].cpu().to(torch.complex128).numpy()
+    per = np.linalg.norm(x - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref)), float(per.max())
+
+
+def step_bytes(info, w, nv, prec):
+    """Algorithmic bytes of one apply: input and output tensors, factors and
+    cores at their stored sizes, and the one mid-level exchange,
+    bd nv (N_in + N_out) + bf (V, W, U, P entries) + bf (core entries)
+    + 2 bd nv min(|F_mid|, |G_mid|)."""
+    bd = 16 if prec == 0 else 8
+    bf = bd
+    mid = min(info["mid_src_entries"], info["mid_tgt_entries"])
+    return bd * nv * 2 * w.N + bf * info["factor_entries"] + bf * info["core_entries"] + 2 * bd * nv * mid
 
 
 def main():
@@ -363,10 +402,26 @@ def main():
                 "tflops": flops_launch / (per_launch_ms * 1e-3) / 1e12,
                 "flop_per_byte": flops_launch / max(bytes_launch, 1),
                 "share_of_step": dom["ms_total"] / max(sum(s["ms_total"] for s in stats), 1e-9)}
+    if roof is not None:
+        b_step = step_bytes(info, w, nv, prec)
+        roof["step_bytes"] = b_step
+        roof["step_achieved"] = b_step / (ms * 1e-3) / 1e9
+        roof["step_frac"] = roof["step_achieved"] / pk["hbm_gbs"]
+    try:
+        fp32_peak = tb.alu_peak(tb.PREC_C64)
+        fp64_peak = tb.alu_peak(tb.PREC_C128)
+    except Exception:
+        fp32_peak = fp64_peak = None
     passes = [{"pass": f'{s["name"]}@l{s["level"]}', "ms": s["ms_total"] / s["launches"],
                "kernels": s["kernels"] // max(s["launches"], 1),
                "GBps": s["bytes"] / (s["ms_total"] / s["launches"] * 1e-3) / 1e9,
                "TFLOPs": s["flops"] / (s["ms_total"] / s["launches"] * 1e-3) / 1e12} for s in stats]
+    alu = fp64_peak if prec == tb.PREC_C128 else fp32_peak
+    for p_ in passes:
+        p_["hbm_frac"] = p_["GBps"] / pk["hbm_gbs"]
+        # CUDA-core passes against the measured FMA peak (the split-BF16 core runs on the tensor cores)
+        if alu and (not p_["pass"].startswith("core") or prec != tb.PREC_C64_SPLITBF16):
+            p_["alu_frac"] = p_["TFLOPs"] / alu
     mode_traffic = level_mode_bytes(info, w, nv, 8 if prec != tb.PREC_C128 else 16)
     for p_ in passes:
         if p_["pass"] in mode_traffic:   # bytes the per-mode launches stream, intermediates included
@@ -400,12 +455,23 @@ def main():
                       "l2": "inputs larger than L2 (no flush)", "graph": True,
                       "autotune_s": tune_s},
            "roofline": roof, "passes": passes, "adjoint": adjoint, "e2e": e2e,
+           "alu_peak": {"fp32_tflops": fp32_peak, "fp64_tflops": fp64_peak, "kind": "measured",
+                        "how": "tb_alu_peak: independent FMA chains on every SM, CUDA-event timed"},
            "gpu_launches": launches_per_step * args.steps}
 
     if rank == 0:
         f_np = f_host.numpy()
+        refs = None
         if args.err_samples > 0:
-            out["rel_err_sampled"] = rel_err_sampled(w, f_np, u, args.err_samples)
+            refs = sampled_reference(w, f_np, args.err_samples)
+            rows, u_ref, cols, v_ref, src = refs
+            e_all, e_max = rel_err_rows(u, nv, rows, u_ref)
+            ea_all, ea_max = rel_err_rows(v, nv, cols, v_ref)
+            out["rel_err_sampled"] = e_all
+            out["rel_err_sampled_max_rhs"] = e_max
+            out["rel_err_adjoint_sampled"] = ea_all
+            out["rel_err_adjoint_max_rhs"] = ea_max
+            out["rel_err_samples"] = {"outputs": int(len(rows)), "rhs": nv, "reference": src}
             out["rel_err_bound"] = w.bound
         if not args.no_fp64 and prec != tb.PREC_C128:
             f64 = f_host.cuda()
@@ -422,8 +488,8 @@ def main():
             stream.synchronize()
             ms64 = e0.elapsed_time(e1) / k64
             out["fp64_plain"] = {"value": N * nv / (ms64 * 1e-3) / 1e9, "ms_per_step": ms64,
-                                 "rel_err_sampled": rel_err_sampled(w, f_np, u64, args.err_samples)
-                                 if args.err_samples > 0 else None}
+                                 "rel_err_sampled": rel_err_rows(u64, nv, refs[0], refs[1])[0]
+                                 if refs is not None else None}
             del f64, u64
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(w, f_np)

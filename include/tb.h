@@ -139,6 +139,9 @@ typedef struct {
     int64_t level_entries_max;     /* largest intermediate (per RHS, padded) */
     int64_t device_bytes;          /* device memory held by the handle */
     double build_seconds;          /* wall time of tb_build */
+    int64_t mid_src_entries;       /* entries of the source-side mid-level tensor F_{t,s} per RHS
+                                      (compact: prod_k |s-bar_k| summed over the pairs) */
+    int64_t mid_tgt_entries;       /* entries of the target-side mid-level tensor G_{t,s} per RHS */
 } tb_info;
 
 /* Fill *opt with the defaults described in tb_options. */
@@ -230,8 +233,9 @@ tb_status tb_apply_host_batch(tb_handle h, const void *const *f, void *const *u,
  *   - The first call on a device looks up the scratch address on the host
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - Every call shares the one scratch area, and it keeps the last call's
- *     contents.  Nothing in it has to start at zero (each pass writes every
- *     entry a later pass reads).  Calls that overlap on the GPU (on different
+ *     contents.  Nothing in it has to start at zero: each pass writes every
+ *     entry that a later pass of the same call reads (the tests check this by
+ *     calling first with an all-NaN input, then with clean ones).  Calls that overlap on the GPU (on different
  *     streams, or from several host threads) race on it and corrupt each
  *     other's results: serialise them.
  *   - No CUDA-graph replay and no per-pass profiling on this path.
@@ -290,6 +294,18 @@ tb_status tb_profile_enable(tb_handle h, int on);
  * record.
  */
 tb_status tb_profile_stats(tb_handle h, tb_pass_stat *stats, int cap, int *count);
+
+/*
+ * Measured arithmetic throughput of the current CUDA device's FMA pipes, for
+ * the ALU roofline of the apply's CUDA-core kernels (the paper has no
+ * counterpart: this is a measurement utility of the library).  Runs a kernel
+ * of independent fused multiply-add chains on every SM (FP32 scalar FFMA for
+ * precision = TB_PREC_C64, FP64 DFMA for TB_PREC_C128), times it with CUDA
+ * events on `cuda_stream` after one warm-up launch, and stores 2 x FMAs / s /
+ * 1e12 in *tflops.  Allocates (and frees) a small device buffer; synchronous.
+ * Errors: TB_EINVAL for a NULL tflops or another precision, TB_ECUDA.
+ */
+tb_status tb_alu_peak(int precision, void *cuda_stream, double *tflops);
 
 /* Release everything the handle owns.  NULL is accepted (TB_OK). */
 tb_status tb_free(tb_handle h);

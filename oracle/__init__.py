@@ -11,6 +11,8 @@ Contents
     grids x = i/n, y = j - n/2, written as the textbook DFT identity
     u = (-1)^(i_1+...+i_d) * fftn(f) (Sec. 3.2.1, DFT paragraph: the d-D DFT is
     a product of 1-D DFTs); a library FFT is the only step.
+  * fourier_fft_adjoint -- the adjoint K^H g of the same operator by the same
+    identity, v = n^d ifftn((-1)^(i_1+...+i_d) g).
   * dense_matrix  -- the full kernel matrix for tiny grids (numpy), used only
     as a brute-force cross-check of the direct sum.
 
@@ -173,6 +175,25 @@ def fourier_fft(f, d: int, sign: int = -1) -> np.ndarray:
         par = par + np.arange(f.shape[k]).reshape(sh)
     s = np.where(par % 2 == 0, 1.0, -1.0)
     return u * s[..., None] if f.ndim == d + 1 else u * s
+
+
+def fourier_fft_adjoint(g, d: int) -> np.ndarray:
+    """Full adjoint output v = K^H g of the Fourier kernel exp(-2 pi i x.y) on the
+    uniform grids x_k = i/n, y_k = j - n/2 (n even), via the DFT identity.
+
+    conj(K[i, j]) = exp(+2 pi i ij/n) (-1)^i, so the sign now sits on the
+    summed (target) index: v = n^d ifftn((-1)^(sum_k i_k) g) over the d leading
+    axes of g (m_1..m_d, nv)."""
+    g = _as_c128(g)
+    axes = tuple(range(d))
+    par = np.zeros(g.shape[:d], dtype=np.int64)
+    for k in range(d):
+        sh = [1] * d
+        sh[k] = g.shape[k]
+        par = par + np.arange(g.shape[k]).reshape(sh)
+    s = np.where(par % 2 == 0, 1.0, -1.0)
+    gs = g * s[..., None] if g.ndim == d + 1 else g * s
+    return np.fft.ifftn(gs, axes=axes) * np.prod([g.shape[a] for a in axes])
 
 
 def dense_matrix(kind, params, xs, ys) -> np.ndarray:

@@ -32,7 +32,8 @@ STATUS = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "TB_ERAN
 # every symbol declared in include/tb.h
 EXPORTS = ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
            "tb_apply_host", "tb_query", "tb_free", "tb_last_error", "tb_version",
-           "tb_profile_enable", "tb_profile_stats", "tb_apply_noalloc", "tb_autotune", "tb_apply_host_batch")
+           "tb_profile_enable", "tb_profile_stats", "tb_apply_noalloc", "tb_autotune", "tb_apply_host_batch",
+           "tb_alu_peak")
 
 
 class TBError(RuntimeError):
@@ -64,7 +65,8 @@ class _Info(ctypes.Structure):
                 ("rank_min", ctypes.c_int), ("rank_max", ctypes.c_int), ("num_ids", ctypes.c_int64),
                 ("core_entries", ctypes.c_int64), ("factor_entries", ctypes.c_int64),
                 ("level_entries_max", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("build_seconds", ctypes.c_double)]
+                ("build_seconds", ctypes.c_double), ("mid_src_entries", ctypes.c_int64),
+                ("mid_tgt_entries", ctypes.c_int64)]
 
 
 class _PassStat(ctypes.Structure):
@@ -108,9 +110,10 @@ def lib():
         L.tb_profile_stats.argtypes = [P, ctypes.POINTER(_PassStat), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         L.tb_apply_noalloc.argtypes = [P, P, P, I64, ctypes.c_int, P]
         L.tb_apply_host_batch.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), I64, I64, ctypes.c_int]
+        L.tb_alu_peak.argtypes = [ctypes.c_int, P, ctypes.POINTER(ctypes.c_double)]
         for name in ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
                      "tb_apply_host", "tb_query", "tb_free", "tb_profile_enable", "tb_profile_stats",
-                     "tb_apply_noalloc", "tb_apply_host_batch"):
+                     "tb_apply_noalloc", "tb_apply_host_batch", "tb_alu_peak"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -194,6 +197,7 @@ class TBOperator:
             "core_entries": inf.core_entries, "factor_entries": inf.factor_entries,
             "level_entries_max": inf.level_entries_max, "device_bytes": inf.device_bytes,
             "build_seconds": inf.build_seconds,
+            "mid_src_entries": inf.mid_src_entries, "mid_tgt_entries": inf.mid_tgt_entries,
         }
 
     def autotune(self, nv: int = 1, precision: int | None = None):
@@ -279,6 +283,16 @@ class TBOperator:
         _check(lib().tb_apply_host(self._h, ctypes.c_void_p(f.ctypes.data), ctypes.c_void_p(u.ctypes.data),
                                    nv, precision))
         return u
+
+
+def alu_peak(precision: int = PREC_C64) -> float:
+    """Measured FMA throughput (TFLOP/s) of the current device: FP32 for PREC_C64,
+    FP64 for PREC_C128 (tb_alu_peak)."""
+    torch = _torch()
+    out = ctypes.c_double()
+    _check(lib().tb_alu_peak(int(precision), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream),
+                             ctypes.byref(out)))
+    return out.value
 
 
 def from_workload(w, **kw) -> TBOperator:

@@ -2,6 +2,8 @@
 // construction orchestration (Alg. 1) and apply orchestration (Alg. 2).
 #include <algorithm>
 #include <chrono>
+#include <climits>
+#include <cstdint>
 #include <cmath>
 #include <cstdio>
 #include <complex>
@@ -25,6 +27,9 @@ static tb_status fail(tb_status s, const std::string &msg) {
     g_err = msg;
     return s;
 }
+
+// The same for entry points defined in other translation units.
+tb_status tb::fail_status(tb_status s, const std::string &msg) { return fail(s, msg); }
 
 #define TB_CK(call)                                                                              \
     do {                                                                                         \
@@ -81,6 +86,16 @@ int64_t prod_tile(const SideLevel &s, int d) {
     int64_t t = 1;
     for (int k = 0; k < d; ++k) t *= s.R[k];
     return t;
+}
+
+// Right-hand-side counts whose tensors (N x nv entries of es bytes) have a
+// byte size representable in size_t and whose level tiles index with int
+// (the kernels take nv as int; level_pass checks the tile sizes).
+tb_status check_nv(int64_t N, int64_t nv, size_t es) {
+    if (nv > (int64_t)INT32_MAX) return fail(TB_EUNSUPPORTED, "nv above 2^31 - 1 is not supported");
+    if (N > 0 && (uint64_t)nv > (uint64_t)(SIZE_MAX / es) / (uint64_t)N)
+        return fail(TB_EINVAL, "N x nv x element size overflows the address space");
+    return TB_OK;
 }
 
 tb_status check_device_ptr(const void *p, const char *what) {
@@ -954,6 +969,18 @@ extern "C" tb_status tb_query(tb_handle h, tb_info *info) {
     info->level_entries_max = h->level_max;
     info->device_bytes = h->device_bytes + (int64_t)h->ws.bytes * 2 + (int64_t)(h->ws.mbytes[0] + h->ws.mbytes[1]);
     info->build_seconds = h->build_seconds;
+    if (h->separable) {
+        int64_t ms = h->P, mt = h->P;
+        for (int k = 0; k < h->d; ++k) {
+            ms *= h->src[h->Lc].R[k];
+            mt *= h->tgt[h->Lc].R[k];
+        }
+        info->mid_src_entries = ms;
+        info->mid_tgt_entries = mt;
+    } else {
+        info->mid_src_entries = h->core_in_entries;
+        info->mid_tgt_entries = h->core_out_entries;
+    }
     return TB_OK;
 }
 
@@ -1605,6 +1632,9 @@ tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t
 }
 
 tb_status ensure_workspace(tb_plan *h, int64_t nv) {
+    const int64_t lm = std::max<int64_t>({h->level_max, h->mode_max[0], h->mode_max[1], 1});
+    if ((uint64_t)nv > (uint64_t)(SIZE_MAX / sizeof(c128)) / (uint64_t)lm)
+        return fail(TB_ENOMEM, "workspace size for nv = " + std::to_string(nv) + " overflows");
     const size_t need = (size_t)h->level_max * (size_t)nv * sizeof(c128);
     const size_t mneed[2] = {(size_t)h->mode_max[0] * (size_t)nv * sizeof(c128),
                              (size_t)h->mode_max[1] * (size_t)nv * sizeof(c128)};
@@ -1765,6 +1795,7 @@ tb_status apply_common(tb_handle h, const void *in, void *out, int64_t nv, int p
     int64_t N = 1;
     for (int k = 0; k < h->d; ++k) N *= h->n[k];
     const size_t es = precision == TB_PREC_C128 ? 16 : 8;
+    TB_TRY(check_nv(N, nv, es));
     const char *a0 = (const char *)in, *b0 = (const char *)out;
     const size_t bytes = (size_t)N * nv * es;
     if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(TB_EINVAL, "input and output overlap");
@@ -1833,11 +1864,12 @@ extern "C" tb_status tb_autotune(tb_handle h, int64_t nv, int precision, void *s
         return fail(TB_EINVAL, "unknown precision");
     if (!(h->precisions & (1u << precision)))
         return fail(TB_EUNSUPPORTED, "handle was built without precision " + std::to_string(precision));
+    int64_t N = 1;
+    for (int k = 0; k < h->d; ++k) N *= h->n[k];
+    TB_TRY(check_nv(N, nv, precision == TB_PREC_C128 ? 16 : 8));
     if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
     TB_TRY(init_device_attrs(h));
     TB_TRY(ensure_workspace(h, nv));
-    int64_t N = 1;
-    for (int k = 0; k < h->d; ++k) N *= h->n[k];
     const size_t bytes = (size_t)N * nv * (precision == TB_PREC_C128 ? 16 : 8);
     void *uin = nullptr, *uout = nullptr;
     TB_CK(cudaMalloc(&uin, bytes));
@@ -1880,6 +1912,17 @@ extern "C" tb_status tb_apply_noalloc(tb_handle h, const void *f, void *u, int64
     int64_t N = 1;
     for (int k = 0; k < h->d; ++k) N *= h->n[k];
     const size_t es = precision == TB_PREC_C128 ? 16 : 8;
+    TB_TRY(check_nv(N, nv, es));
+    // reject by division first, so that no product below can wrap: the
+    // scratch needs (2 level tensors + 2 mode intermediates) x nv x es bytes
+    {
+        const uint64_t per_rhs =
+            (uint64_t)es * (2 * (uint64_t)h->level_max + (uint64_t)h->mode_max[0] + (uint64_t)h->mode_max[1]);
+        if (per_rhs > 0 && (uint64_t)nv > (uint64_t)TB_NOALLOC_SCRATCH_BYTES / per_rhs)
+            return fail(TB_EUNSUPPORTED, "tb_apply_noalloc: nv = " + std::to_string(nv) + " needs " +
+                                             std::to_string(per_rhs) + " bytes of scratch per RHS; the fixed scratch holds " +
+                                             std::to_string((size_t)TB_NOALLOC_SCRATCH_BYTES) + " (reduce nv)");
+    }
     const char *a0 = (const char *)f, *b0 = (const char *)u;
     if (a0 < b0 + (size_t)N * nv * es && b0 < a0 + (size_t)N * nv * es)
         return fail(TB_EINVAL, "input and output overlap");
@@ -1930,6 +1973,7 @@ extern "C" tb_status tb_apply_host(tb_handle h, const void *f, void *u, int64_t 
     int64_t N = 1;
     for (int k = 0; k < h->d; ++k) N *= h->n[k];
     const size_t es = precision == TB_PREC_C128 ? 16 : 8;
+    TB_TRY(check_nv(N, nv, es));
     const size_t bytes = (size_t)N * nv * es;
     if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
     if (bytes > h->ws.host_bytes) {
@@ -1957,6 +2001,7 @@ extern "C" tb_status tb_apply_host_batch(tb_handle h, const void *const *f, void
         if (!f[i] || !u[i]) return fail(TB_EINVAL, "f[i] and u[i] must be non-NULL");
     int64_t N = 1;
     for (int k = 0; k < h->d; ++k) N *= h->n[k];
+    TB_TRY(check_nv(N, nv, precision == TB_PREC_C128 ? 16 : 8));
     const size_t bytes = (size_t)N * nv * (precision == TB_PREC_C128 ? 16 : 8);
     if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
     HostPipe &P = h->pipe;

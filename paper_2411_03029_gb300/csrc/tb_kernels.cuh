@@ -1,9 +1,14 @@
 // Argument blocks and launchers of the construction and apply kernels.
 #pragma once
 
+#include <string>
+
 #include "tb_common.cuh"
 
 namespace tb {
+
+// Record `msg` as the calling thread's tb_last_error() and return s.
+tb_status fail_status(tb_status s, const std::string &msg);
 
 // ------------------------------------------------------------- construction
 struct IdArgs {

@@ -59,6 +59,14 @@ def test_fourier_bitrev_is_exact(d, n, L, separable):
     assert rel(v, oracle.workload_apply_adjoint(w, f)) < 1e-12
     u32 = run(op, w, f, tb.PREC_C64)
     assert rel(u32, ref) < 2e-6
+    if separable == 0 and d > 1:
+        # exact ranks: the butterfly itself is exact, so what remains is the
+        # rounding of the split-BF16 core (two BF16 terms per value and per core
+        # entry, about 16 bits, FP32 accumulation) plus the FP32 level passes
+        ubf = run(op, w, f, tb.PREC_C64_SPLITBF16)
+        assert rel(ubf, ref) < 5e-5, rel(ubf, ref)
+        vbf = run(op, w, f, tb.PREC_C64_SPLITBF16, adjoint=True)
+        assert rel(vbf, oracle.workload_apply_adjoint(w, f)) < 5e-5
 
 
 @pytest.mark.parametrize("d,n,L,nv", [(4, 8, 2, 3), (6, 4, 2, 2)])
@@ -72,19 +80,6 @@ def test_separable_high_dimension_full_output(d, n, L, nv):
     assert rel(run(op, w, f, tb.PREC_C128), ref) < 1e-12
     assert rel(run(op, w, f, tb.PREC_C64), ref) < 1e-5
     assert rel(run(op, w, f, tb.PREC_C128, adjoint=True), oracle.workload_apply_adjoint(w, f)) < 1e-12
-
-
-def test_config_fourier6d_n16_sampled():
-    w = W.WORKLOADS["fourier6d_n16"]
-    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C128))
-    f = W.rhs(w)
-    rows = W.sample_targets(w, 128)
-    ref = oracle.workload_apply(w, f, rows)
-    u = run(op, w, f, tb.PREC_C64, rows)
-    assert rel(u, ref) <= w.bound
-    assert rel(run(op, w, f, tb.PREC_C128, rows), ref) < 1e-12
-    cols = W.sample_targets(w, 64, seed=77)
-    assert rel(run(op, w, f, tb.PREC_C64, cols, adjoint=True), oracle.workload_apply_adjoint(w, f, cols)) <= w.bound
 
 
 def test_config_fourier2d_n64_full_output():
@@ -235,28 +230,6 @@ def test_splitbf16_core_multilevel_and_deterministic():
     assert rel(ubf[rows], oracle.workload_apply(w, f, rows)) <= w.bound
     again = run(op, w, f, tb.PREC_C64_SPLITBF16)
     assert np.array_equal(ubf, again)
-
-
-# ------------------------------------------------------- benchmark workloads
-def test_config_helmholtz3d_n64_sampled():
-    w = W.WORKLOADS["helmholtz3d_n64"]
-    op = tb.from_workload(w)
-    f = W.rhs(w)
-    rows = W.sample_targets(w, 1024)
-    ref = oracle.workload_apply(w, f, rows)
-    assert rel(run(op, w, f, tb.PREC_C64, rows), ref) <= w.bound
-    assert rel(run(op, w, f, tb.PREC_C128, rows), ref) <= 10 * w.tol
-
-
-def test_config_radon2d_n256_sampled():
-    w = W.WORKLOADS["radon2d_n256"]
-    op = tb.from_workload(w)
-    f = W.rhs(w)
-    rows = W.sample_targets(w, 2048)
-    ref = oracle.workload_apply(w, f, rows)
-    assert rel(run(op, w, f, tb.PREC_C64, rows), ref) <= w.bound
-    refv = oracle.workload_apply_adjoint(w, f, rows)
-    assert rel(run(op, w, f, tb.PREC_C64, rows, adjoint=True), refv) <= w.bound
 
 
 # ------------------------------------------- register-resident separable chains

@@ -61,6 +61,25 @@ def test_fourier_direct_sum_is_dft(d, n, nv):
     assert _rel(u, ref) < 1e-12
 
 
+@pytest.mark.parametrize("d,n,nv", [(1, 16, 2), (2, 8, 3), (3, 4, 1), (6, 4, 2)])
+def test_fourier_adjoint_direct_sum_is_inverse_dft(d, n, nv):
+    # v = K^H g with the sign of the DFT identity on the summed index
+    xs, ys = _grid(W.FOURIER, d, n)
+    g = _rand((n,) * d + (nv,), 40 + d)
+    v = oracle.apply_adjoint(W.FOURIER, (), xs, ys, g).reshape(g.shape)
+    assert _rel(v, oracle.fourier_fft_adjoint(g, d)) < 1e-12
+
+
+def test_fourier_fft_adjoint_against_explicit_loops():
+    # v[j] = sum_i exp(+2 pi i (i/n)(j - n/2)) g[i] for d = 1
+    n = 10
+    g = _rand((n, 1), 6)
+    v = oracle.fourier_fft_adjoint(g, 1)
+    ref = np.array([sum(np.exp(2j * math.pi * (i / n) * (j - n / 2)) * g[i, 0] for i in range(n))
+                    for j in range(n)])
+    assert _rel(v[:, 0], ref) < 1e-13
+
+
 def test_fourier_fft_against_numpy_definition():
     # u[i] = sum_j exp(-2 pi i (i/n)(j - n/2)) f[j] for d = 1, by explicit loops
     n = 12
