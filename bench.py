@@ -334,7 +334,12 @@ def main():
             for _ in range(args.warmup + args.steps):
                 op.apply(f, prec, out=u)
         stream.synchronize()
-        print(json.dumps({"profile_only": True, "workload": w.name}))
+        # sizes for scaling counter captures of this (possibly reduced) copy to the full workload
+        core_bytes = 8 * info["core_entries"] + 8 * nv * (info["mid_src_entries"] + info["mid_tgt_entries"])
+        print(json.dumps({"profile_only": True, "workload": w.name, "n": w.n, "nv": nv,
+                          "core_entries": info["core_entries"], "mid_src_entries": info["mid_src_entries"],
+                          "mid_tgt_entries": info["mid_tgt_entries"], "core_pass_bytes_c64": core_bytes,
+                          "ranks_src": info["rank_src"], "ranks_tgt": info["rank_tgt"]}))
         return
 
     # ---------------------------------------------------- timed region (graph replay)

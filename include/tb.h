@@ -246,6 +246,37 @@ tb_status tb_apply_noalloc(tb_handle h, const void *f, void *u, int64_t nv, int 
                            void *cuda_stream);
 
 /*
+ * Least-squares solve on the device: for each right-hand-side column,
+ * min_x ||K x - b||_2 by CGLS (conjugate gradients on the normal equations
+ * K^H K x = K^H b), with the forward (tb_apply) and adjoint (tb_apply_adjoint)
+ * butterflies as the operator.  This is the inversion of Radon-type data that
+ * the paper motivates its generalized Radon kernels with (Sec. 4.2); the
+ * paper itself gives no solver.
+ *   b       device pointer, target-grid tensor (m_1..m_d, nv), apply layout
+ *   x       device pointer, source-grid tensor (n_1..n_d, nv): the starting
+ *           point on entry (zero it for x0 = 0), the iterate after `iters`
+ *           iterations on return
+ *   iters   CGLS iterations (>= 0)
+ *   use_graph  1 = capture one iteration (two applies, the vector updates and
+ *           the norms) as a CUDA graph once and replay it `iters` times; every
+ *           scalar of the iteration stays in device memory, so no iteration
+ *           waits on the host.  Needs a stream other than the legacy default
+ *           stream (NULL runs eagerly)
+ *   resid   NULL or host array of (iters + 1) x nv doubles: ||b - K x_k||_2 of
+ *           each column after k iterations (row k), row 0 the start
+ * Synchronous: returns when x and resid are final.  Allocates four N x nv
+ * work tensors and small scalar arrays for the call and frees them on return;
+ * the applies use the handle's workspaces (as tb_apply).  Columns whose
+ * residual or search direction becomes exactly zero stop moving (alpha = 0,
+ * beta = 0).  Reductions are deterministic (fixed summation order).
+ * Errors: TB_EINVAL (NULL or overlapping b / x, nv < 1, iters < 0, called
+ * inside a stream capture), TB_EUNSUPPORTED (precision not built, nv > 1024),
+ * TB_ENOMEM, TB_ECUDA.
+ */
+tb_status tb_cgls(tb_handle h, const void *b, void *x, int64_t nv, int iters, int precision, int use_graph,
+                  double *resid, void *cuda_stream);
+
+/*
  * Empirical tuning of the apply's launch shapes for nv right-hand sides at
  * `precision`, on the handle's own factors and workspaces (the paper fixes no
  * launch layout; this is the library's own schedule search):

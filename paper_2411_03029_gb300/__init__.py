@@ -33,7 +33,7 @@ STATUS = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "TB_ERAN
 EXPORTS = ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
            "tb_apply_host", "tb_query", "tb_free", "tb_last_error", "tb_version",
            "tb_profile_enable", "tb_profile_stats", "tb_apply_noalloc", "tb_autotune", "tb_apply_host_batch",
-           "tb_alu_peak")
+           "tb_alu_peak", "tb_cgls")
 
 
 class TBError(RuntimeError):
@@ -111,9 +111,10 @@ def lib():
         L.tb_apply_noalloc.argtypes = [P, P, P, I64, ctypes.c_int, P]
         L.tb_apply_host_batch.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), I64, I64, ctypes.c_int]
         L.tb_alu_peak.argtypes = [ctypes.c_int, P, ctypes.POINTER(ctypes.c_double)]
+        L.tb_cgls.argtypes = [P, P, P, I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
         for name in ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
                      "tb_apply_host", "tb_query", "tb_free", "tb_profile_enable", "tb_profile_stats",
-                     "tb_apply_noalloc", "tb_apply_host_batch", "tb_alu_peak"):
+                     "tb_apply_noalloc", "tb_apply_host_batch", "tb_alu_peak", "tb_cgls"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -255,6 +256,24 @@ class TBOperator:
     def apply_adjoint(self, g, precision: int | None = None, out=None):
         """v = K^H g on the current torch stream (tb_apply_adjoint)."""
         return self._run(lib().tb_apply_adjoint, g, precision, out)
+
+    def cgls(self, b, iters: int, x0=None, precision: int | None = None, graph: bool = True):
+        """Least squares min_x ||K x - b|| per RHS column by CGLS on the device (tb_cgls).
+
+        b: CUDA tensor of the target-grid shape (+ nv); x0: start (zeros if None).
+        Returns (x, resid) with resid[k, v] = ||b - K x_k|| of column v after k
+        iterations (numpy, (iters + 1) x nv).  With graph=True one iteration is
+        captured as a CUDA graph and replayed on the current stream."""
+        torch = _torch()
+        b, precision, squeeze = self._prep(b, precision)
+        nv = b.shape[-1]
+        x = torch.zeros_like(b) if x0 is None else self._prep(x0, precision)[0].clone()
+        resid = np.zeros((iters + 1, nv), dtype=np.float64)
+        stream = torch.cuda.current_stream(b.device).cuda_stream
+        _check(lib().tb_cgls(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), nv,
+                             int(iters), precision, int(graph), ctypes.c_void_p(resid.ctypes.data),
+                             ctypes.c_void_p(stream)))
+        return (x.squeeze(-1) if squeeze else x), resid
 
     def apply_host_batch(self, fs, us, precision: int | None = None):
         """u_i = K f_i for lists of host arrays (numpy, pinned for overlap), with the

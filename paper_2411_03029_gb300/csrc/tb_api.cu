@@ -1890,6 +1890,123 @@ extern "C" tb_status tb_autotune(tb_handle h, int64_t nv, int precision, void *s
     return s;
 }
 
+// ------------------------------------------------- least squares (CGLS)
+namespace {
+
+// Device buffers of one tb_cgls call.
+struct CglsWork {
+    void *r = nullptr, *s = nullptr, *p = nullptr, *q = nullptr;
+    double *partial = nullptr, *hist = nullptr;
+    CglsScalars *sc = nullptr;
+    int *count = nullptr;
+    ~CglsWork() {
+        for (void *ptr : {r, s, p, q, (void *)partial, (void *)hist, (void *)sc, (void *)count})
+            if (ptr) cudaFree(ptr);
+    }
+};
+
+template <class R>
+tb_status cgls_impl(tb_plan *h, const void *b, void *x, int64_t nv, int iters, int precision, bool graph,
+                    double *resid, cudaStream_t st) {
+    int64_t N = 1;
+    for (int k = 0; k < h->d; ++k) N *= h->n[k];
+    const size_t bytes = (size_t)N * nv * sizeof(cx<R>);
+    CglsWork w;
+    for (void **ptr : {&w.r, &w.s, &w.p, &w.q}) TB_CK(cudaMalloc(ptr, bytes));
+    TB_CK(cudaMalloc(&w.partial, (size_t)cgls_blocks() * nv * sizeof(double)));
+    TB_CK(cudaMalloc(&w.hist, (size_t)(iters + 1) * nv * sizeof(double)));
+    TB_CK(cudaMalloc(&w.sc, (size_t)nv * sizeof(CglsScalars)));
+    TB_CK(cudaMalloc(&w.count, sizeof(int)));
+    TB_CK(cudaMemsetAsync(w.sc, 0, (size_t)nv * sizeof(CglsScalars), st));
+    TB_CK(cudaMemsetAsync(w.count, 0, sizeof(int), st));
+    TB_CK(cudaMemsetAsync(w.hist, 0, (size_t)(iters + 1) * nv * sizeof(double), st));
+    cx<R> *X = (cx<R> *)x, *Rr = (cx<R> *)w.r, *S = (cx<R> *)w.s, *Pp = (cx<R> *)w.p, *Q = (cx<R> *)w.q;
+    const cx<R> *B = (const cx<R> *)b;
+    const int cap = iters + 1;
+    // start: r = b - K x0, s = K^H r, p = s, gamma = ||s||^2 (eager; it also sets
+    // every kernel's attributes before any capture)
+    TB_TRY(run_chain<R>(h, false, X, Q, nv, st, false, precision));
+    TB_CK(launch_cgls_sub<R>(Rr, B, Q, N, (int)nv, w.partial, st));
+    TB_CK(launch_cgls_finalize(w.partial, (int)nv, CG_RESID, w.sc, w.hist, w.count, cap, st));
+    TB_TRY(run_chain<R>(h, true, Rr, S, nv, st, false, precision));
+    TB_CK(launch_cgls_sqnorm<R>(S, N, (int)nv, w.partial, st));
+    TB_CK(launch_cgls_finalize(w.partial, (int)nv, CG_GAMMA0, w.sc, w.hist, w.count, cap, st));
+    TB_CK(cudaMemcpyAsync(Pp, S, bytes, cudaMemcpyDeviceToDevice, st));
+    // one iteration: q = K p, alpha = gamma / ||q||^2, x += alpha p, r -= alpha q,
+    // s = K^H r, beta = ||s||^2 / gamma, p = s + beta p, record ||r||
+    auto iteration = [&]() -> tb_status {
+        TB_TRY(run_chain<R>(h, false, Pp, Q, nv, st, false, precision));
+        TB_CK(launch_cgls_sqnorm<R>(Q, N, (int)nv, w.partial, st));
+        TB_CK(launch_cgls_finalize(w.partial, (int)nv, CG_ALPHA, w.sc, w.hist, w.count, cap, st));
+        TB_CK(launch_cgls_xr<R>(X, Rr, Pp, Q, w.sc, N, (int)nv, w.partial, st));
+        TB_CK(launch_cgls_finalize(w.partial, (int)nv, CG_RESID, w.sc, w.hist, w.count, cap, st));
+        TB_TRY(run_chain<R>(h, true, Rr, S, nv, st, false, precision));
+        TB_CK(launch_cgls_sqnorm<R>(S, N, (int)nv, w.partial, st));
+        TB_CK(launch_cgls_finalize(w.partial, (int)nv, CG_BETA, w.sc, w.hist, w.count, cap, st));
+        TB_CK(launch_cgls_p<R>(Pp, S, w.sc, N, (int)nv, st));
+        return TB_OK;
+    };
+    if (graph && iters > 0) {
+        cudaGraph_t g;
+        TB_CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        tb_status s = iteration();
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (s != TB_OK) return s;
+        if (e != cudaSuccess) return fail(TB_ECUDA, std::string("tb_cgls capture: ") + cudaGetErrorString(e));
+        cudaGraphExec_t exec;
+        e = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(TB_ECUDA, std::string("tb_cgls instantiate: ") + cudaGetErrorString(e));
+        cudaError_t le = cudaSuccess;
+        for (int it = 0; it < iters && le == cudaSuccess; ++it) le = cudaGraphLaunch(exec, st);
+        cudaError_t se = cudaStreamSynchronize(st);
+        cudaGraphExecDestroy(exec);
+        if (le != cudaSuccess) return fail(TB_ECUDA, std::string("tb_cgls replay: ") + cudaGetErrorString(le));
+        if (se != cudaSuccess) return fail(TB_ECUDA, std::string("tb_cgls: ") + cudaGetErrorString(se));
+    } else {
+        for (int it = 0; it < iters; ++it) TB_TRY(iteration());
+    }
+    if (resid) TB_CK(cudaMemcpyAsync(resid, w.hist, (size_t)(iters + 1) * nv * sizeof(double), cudaMemcpyDeviceToHost, st));
+    TB_CK(cudaStreamSynchronize(st));
+    return TB_OK;
+}
+
+}  // namespace
+
+extern "C" tb_status tb_cgls(tb_handle h, const void *b, void *x, int64_t nv, int iters, int precision,
+                             int use_graph, double *resid, void *stream) {
+    if (!h) return fail(TB_EINVAL, "handle is NULL");
+    if (nv <= 0) return fail(TB_EINVAL, "nv must be positive");
+    if (iters < 0) return fail(TB_EINVAL, "iters must be >= 0");
+    if (nv > cgls_max_nv()) return fail(TB_EUNSUPPORTED, "tb_cgls supports nv <= " + std::to_string(cgls_max_nv()));
+    if (precision < TB_PREC_C128 || precision > TB_PREC_C64_SPLITBF16)
+        return fail(TB_EINVAL, "unknown precision");
+    if (!(h->precisions & (1u << precision)))
+        return fail(TB_EUNSUPPORTED, "handle was built without precision " + std::to_string(precision));
+    TB_TRY(check_device_ptr(b, "b"));
+    TB_TRY(check_device_ptr(x, "x"));
+    int64_t N = 1;
+    for (int k = 0; k < h->d; ++k) N *= h->n[k];
+    const size_t es = precision == TB_PREC_C128 ? 16 : 8;
+    TB_TRY(check_nv(N, nv, es));
+    const char *a0 = (const char *)b, *b0 = (const char *)x;
+    if (a0 < b0 + (size_t)N * nv * es && b0 < a0 + (size_t)N * nv * es)
+        return fail(TB_EINVAL, "b and x overlap");
+    if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
+    TB_TRY(init_device_attrs(h));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    TB_CK(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return fail(TB_EINVAL, "tb_cgls cannot run inside a stream capture");
+    TB_TRY(ensure_workspace(h, nv));
+    // launch-shape tuning on temporary buffers, so that x keeps the caller's start
+    if (h->autotune && !is_tuned(h, nv, precision)) TB_TRY(tb_autotune(h, nv, precision, stream));
+    // graphs need a capturable stream: the legacy default stream is not one
+    const bool graph = use_graph != 0 && st != nullptr;
+    if (precision == TB_PREC_C128) return cgls_impl<double>(h, b, x, nv, iters, precision, graph, resid, st);
+    return cgls_impl<float>(h, b, x, nv, iters, precision, graph, resid, st);
+}
+
 // ------------------------------------------------- apply without allocating
 // The scratch area of tb_apply_noalloc: a fixed device array compiled into the
 // library.  In host code `g_noalloc_scratch` names a host-side stand-in, not

@@ -364,6 +364,27 @@ cudaError_t launch_sep_reg2(bool adjoint, const SepReg2Args<R> &a, cudaStream_t 
 template <class R>
 bool sep_reg_supported(int lc, int rk);
 
+// Least-squares solver (tb_cgls, tb_cgls.cu): per-column scalars of the CGLS
+// iteration, kept in device memory.
+struct CglsScalars {
+    double gamma, delta, alpha, beta;
+};
+enum CglsMode : int { CG_GAMMA0 = 0, CG_ALPHA = 1, CG_BETA = 2, CG_RESID = 3 };
+int cgls_blocks();   // rows of the partial-sum arrays (blocks of the vector kernels)
+int cgls_max_nv();
+template <class R>
+cudaError_t launch_cgls_sqnorm(const cx<R> *a, int64_t rows, int nv, double *partial, cudaStream_t st);
+template <class R>
+cudaError_t launch_cgls_xr(cx<R> *x, cx<R> *r, const cx<R> *p, const cx<R> *q, const CglsScalars *sc, int64_t rows,
+                           int nv, double *partial, cudaStream_t st);
+template <class R>
+cudaError_t launch_cgls_sub(cx<R> *r, const cx<R> *b, const cx<R> *q, int64_t rows, int nv, double *partial,
+                            cudaStream_t st);
+template <class R>
+cudaError_t launch_cgls_p(cx<R> *p, const cx<R> *s, const CglsScalars *sc, int64_t rows, int nv, cudaStream_t st);
+cudaError_t launch_cgls_finalize(const double *partial, int nv, int mode, CglsScalars *sc, double *hist, int *count,
+                                 int cap, cudaStream_t st);
+
 enum class Pass { LeafIn, Split, Gather, LeafOut };
 
 template <class R>

@@ -137,3 +137,12 @@ def test_build_rejects_bad_kernel_parameters_without_touching_the_gpu(lib):
                         ctypes.byref(h)) == 1
     assert b"coincides" in lib.tb_last_error()
     assert not h.value
+
+
+def test_cgls_and_alu_peak_reject_bad_arguments_without_touching_the_gpu(lib):
+    assert lib.tb_cgls(None, None, None, 1, 5, tb.PREC_C64, 1, None, None) == 1      # NULL handle
+    assert b"handle" in lib.tb_last_error()
+    out = ctypes.c_double()
+    assert lib.tb_alu_peak(tb.PREC_C64, None, None) == 1                            # NULL result
+    assert lib.tb_alu_peak(tb.PREC_C64_SPLITBF16, None, ctypes.byref(out)) == 1     # no FMA pipe of its own
+    assert b"precision" in lib.tb_last_error()

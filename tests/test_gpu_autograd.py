@@ -147,3 +147,49 @@ def test_least_squares_iterations_replay_as_one_cuda_graph(radon):
     r0 = torch.linalg.vector_norm(b).item()
     assert torch.linalg.vector_norm(st["r"]).item() < 1e-2 * r0
     assert (torch.linalg.vector_norm(st["x"] - eager["x"]) / torch.linalg.vector_norm(eager["x"])).item() < 1e-4
+
+
+def test_cgls_library_call_graph_and_eager(radon):
+    """tb_cgls: the least-squares solve as one library call, device-resident.
+    The graph-replayed and the eager iterations run the same kernels in the same
+    order (bit-identical), agree with the torch-driven iterations above, and the
+    recorded residual history starts at ||b||, never increases and ends below
+    1e-2 ||b|| after 15 iterations."""
+    w, op = radon
+    f_true = W.smooth_bumps(w).to(torch.complex64).cuda()
+    b = op.apply(f_true)
+    iters = 15
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        xg, rg = op.cgls(b, iters, graph=True)
+        xe, re_ = op.cgls(b, iters, graph=False)
+    side.synchronize()
+    assert torch.equal(xg, xe) and np.array_equal(rg, re_)
+    ref = _cgls_state(op, b)
+    for _ in range(iters):
+        _cgls_step(op, ref)
+    assert (torch.linalg.vector_norm(xg - ref["x"]) / torch.linalg.vector_norm(ref["x"])).item() < 1e-4
+    bn = torch.linalg.vector_norm(b.to(torch.complex128)).item()
+    assert abs(rg[0, 0] - bn) <= 1e-6 * bn
+    assert np.all(np.diff(rg[:, 0]) <= 1e-6 * bn)
+    assert rg[-1, 0] < 1e-2 * bn
+    # the last recorded residual is the residual of the returned iterate
+    true_r = torch.linalg.vector_norm((b - op.apply(xg)).to(torch.complex128)).item()
+    assert abs(true_r - rg[-1, 0]) <= 1e-3 * rg[-1, 0] + 1e-6 * bn
+
+
+def test_cgls_columns_are_independent(radon):
+    """Several RHS columns solve independent systems: each column of a 3-column
+    solve equals the 1-column solve of that column, and a zero column stays zero
+    (alpha = beta = 0, no NaN)."""
+    w, op = radon
+    f_true = W.smooth_bumps(w).to(torch.complex64).cuda()
+    b1 = op.apply(f_true)
+    b3 = torch.cat([b1, 2.5j * b1, torch.zeros_like(b1)], dim=-1).contiguous()
+    x3, r3 = op.cgls(b3, 8)
+    x1, r1 = op.cgls(b1, 8)
+    assert (torch.linalg.vector_norm(x3[..., :1] - x1) / torch.linalg.vector_norm(x1)).item() < 1e-5
+    assert (torch.linalg.vector_norm(x3[..., 1:2] - 2.5j * x1) / torch.linalg.vector_norm(x1)).item() < 1e-5
+    assert torch.count_nonzero(x3[..., 2]).item() == 0 and np.all(r3[:, 2] == 0)
+    assert np.allclose(r3[:, 0], r1[:, 0], rtol=1e-5)
