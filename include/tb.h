@@ -295,6 +295,47 @@ tb_status tb_cgls(tb_handle h, const void *b, void *x, int64_t nv, int iters, in
  */
 tb_status tb_autotune(tb_handle h, int64_t nv, int precision, void *cuda_stream);
 
+/*
+ * Export of a built (non-separable) tensor butterfly, for checking the apply
+ * step by step against an independent implementation of Alg. 2 (the paper has
+ * no counterpart: a debugging interface).  All outputs are host memory;
+ * calls with every array NULL only report the sizes; the copies are
+ * synchronous.  TB_EUNSUPPORTED for separable handles.
+ *
+ * Index conventions (paper notation of Sec. 3.2 / Alg. 1):
+ *   - A multi-set at level l has one node index per mode, i_k in [0, 2^l); its
+ *     flat index is sum_k i_k 2^(l (d-1-k)) (mode 0 most significant).
+ *     Node i at level l of mode k covers tree positions [i n_k / 2^l,
+ *     (i+1) n_k / 2^l); tree position p is grid index perm_k[p]
+ *     (tb_export_order).
+ *   - tb_export_factors(side, level l, mode k): the blocks of
+ *       side 0: V^{s,k}_{tau,nu} (l = 0) and W^{s,k}_{tau,nu} (l > 0),
+ *       side 1: U^{t,k}_{tau,nu} (l = 0) and P^{t,k}_{tau,nu} (l > 0),
+ *     block j = ((S 2^(d l) + T) 2^(Lc-l)) + q with S the flat mid-level
+ *     multi-set of the side (s or t), T the flat level-l multi-set of the
+ *     other tree (tau or nu) and q the node of mode k at depth Lc - l below
+ *     S_k (nu for side 0, tau for side 1).  Each block is rows x cols complex128,
+ *     row-major, rows = padded rank R_{l,k} (row a < ranks[j] is the a-th
+ *     skeleton in pivot order, later rows are zero), cols = C_b,k (l = 0: the
+ *     points of the leaf q in tree order) or 2 R_{l-1,k} (l > 0: the skeletons
+ *     of the children 2q in [0, R_{l-1,k}) and 2q + 1 in [R_{l-1,k}, 2 R_{l-1,k}),
+ *     each in its own pivot order, zero past the child's rank; the children's
+ *     blocks are those of the parent multi-set p_T at level l - 1).
+ *     skel[j * rows + a]: grid index along mode k of skeleton a (-1 past the rank).
+ *     The source side applies a block as out = A in (contracting its columns),
+ *     the target side as out = A^T in.
+ *   - tb_export_cores: pair p = t nF + s (nF = 2^(d Lc)); dims[p * 2d + k] =
+ *     |t-bar_k|, dims[p * 2d + d + k] = |s-bar_k| (the ranks of the level-Lc
+ *     blocks of the pair); entries offsets[p] .. offsets[p+1] hold K(t-bar, s-bar)
+ *     row-major, rows = target multi-index (C order over the modes), columns =
+ *     source multi-index, complex128 (the complex64 cores widened when the
+ *     handle was built without complex128).
+ */
+tb_status tb_export_factors(tb_handle h, int side, int level, int mode, int64_t *count, int *rows, int *cols,
+                            int *ranks, int *skel, void *blocks);
+tb_status tb_export_cores(tb_handle h, int64_t *pairs, int64_t *entries, int64_t *offsets, int *dims, void *core);
+tb_status tb_export_order(tb_handle h, int axis, int *perm);
+
 /* Describe a built handle (ranks, sizes, timings). */
 tb_status tb_query(tb_handle h, tb_info *info);
 

@@ -14,7 +14,11 @@ Contents
   * fourier_fft_adjoint -- the adjoint K^H g of the same operator by the same
     identity, v = n^d ifftn((-1)^(i_1+...+i_d) g).
   * dense_matrix  -- the full kernel matrix for tiny grids (numpy), used only
-    as a brute-force cross-check of the direct sum.
+    as a brute-force cross-check of the direct sum; kernel_matrix, the same
+    formulas at arbitrary point sets.
+  * butterfly     -- the tensor butterfly applied step by step from exported
+    factors (Alg. 2 and Eq. butterfly_tensor), for checking the GPU apply to
+    rounding; see oracle/butterfly.py.
 
 Every function here is pinned by tests/test_oracle.py against closed forms,
 hand-derived special values (tests/golden/), symmetry identities and brute
@@ -201,7 +205,23 @@ def dense_matrix(kind, params, xs, ys) -> np.ndarray:
     d = len(xs)
     X = np.stack(np.meshgrid(*xs, indexing="ij"), -1).reshape(-1, d)
     Y = np.stack(np.meshgrid(*ys, indexing="ij"), -1).reshape(-1, d)
-    Xe, Ye = X[:, None, :], Y[None, :, :]
+    return kernel_matrix(kind, params, X, Y)
+
+
+def kernel_matrix(kind, params, X, Y) -> np.ndarray:
+    """K[i, j] = K(X[i], Y[j]) for point arrays X (m x d) and Y (n x d), in numpy."""
+    X = np.asarray(X, dtype=np.float64)
+    Y = np.asarray(Y, dtype=np.float64)
+    return _kernel(kind, params, X[:, None, :], Y[None, :, :])
+
+
+def kernel_pairs(kind, params, X, Y) -> np.ndarray:
+    """K(X[i], Y[i]) for point arrays X, Y of the same shape (... x d), in numpy."""
+    return _kernel(kind, params, np.asarray(X, dtype=np.float64), np.asarray(Y, dtype=np.float64))
+
+
+def _kernel(kind, params, Xe, Ye) -> np.ndarray:
+    """The kernel formulas on broadcast point arrays (last axis = the d coordinates)."""
     if kind == 1:
         return np.exp(-2j * np.pi * (Xe * Ye).sum(-1))
     if kind == 2:

@@ -33,7 +33,8 @@ STATUS = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "TB_ERAN
 EXPORTS = ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
            "tb_apply_host", "tb_query", "tb_free", "tb_last_error", "tb_version",
            "tb_profile_enable", "tb_profile_stats", "tb_apply_noalloc", "tb_autotune", "tb_apply_host_batch",
-           "tb_alu_peak", "tb_cgls")
+           "tb_alu_peak", "tb_cgls",
+           "tb_export_factors", "tb_export_cores", "tb_export_order")
 
 
 class TBError(RuntimeError):
@@ -112,9 +113,13 @@ def lib():
         L.tb_apply_host_batch.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P), I64, I64, ctypes.c_int]
         L.tb_alu_peak.argtypes = [ctypes.c_int, P, ctypes.POINTER(ctypes.c_double)]
         L.tb_cgls.argtypes = [P, P, P, I64, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P]
+        L.tb_export_factors.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]
+        L.tb_export_cores.argtypes = [P, P, P, P, P, P]
+        L.tb_export_order.argtypes = [P, ctypes.c_int, P]
         for name in ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
                      "tb_apply_host", "tb_query", "tb_free", "tb_profile_enable", "tb_profile_stats",
-                     "tb_apply_noalloc", "tb_apply_host_batch", "tb_alu_peak", "tb_cgls"):
+                     "tb_apply_noalloc", "tb_apply_host_batch", "tb_alu_peak", "tb_cgls",
+                     "tb_export_factors", "tb_export_cores", "tb_export_order"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -274,6 +279,43 @@ class TBOperator:
                              int(iters), precision, int(graph), ctypes.c_void_p(resid.ctypes.data),
                              ctypes.c_void_p(stream)))
         return (x.squeeze(-1) if squeeze else x), resid
+
+    def export(self) -> dict:
+        """The built butterfly as host arrays (tb_export_factors / _cores / _order):
+        {"d", "L", "Lc", "n", "cb", "perm": [d int arrays],
+         "factors": {(side, level, mode): {"ranks", "skel", "blocks"}},
+         "core_offsets", "core_dims", "core"}.  See include/tb.h for the indexing."""
+        L_ = lib()
+        inf = self.info()
+        d, Lc = inf["d"], inf["Lc"]
+        out = {"d": d, "L": inf["L"], "Lc": Lc, "n": inf["n"], "cb": inf["cb"], "perm": [], "factors": {}}
+        for k in range(d):
+            perm = np.zeros(inf["n"][k], dtype=np.int32)
+            _check(L_.tb_export_order(self._h, k, ctypes.c_void_p(perm.ctypes.data)))
+            out["perm"].append(perm)
+        cnt, rows, cols = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+        for side in (0, 1):
+            for lvl in range(Lc + 1):
+                for k in range(d):
+                    _check(L_.tb_export_factors(self._h, side, lvl, k, ctypes.byref(cnt), ctypes.byref(rows),
+                                                ctypes.byref(cols), None, None, None))
+                    ranks = np.zeros(cnt.value, dtype=np.int32)
+                    skel = np.zeros((cnt.value, rows.value), dtype=np.int32)
+                    blocks = np.zeros((cnt.value, rows.value, cols.value), dtype=np.complex128)
+                    _check(L_.tb_export_factors(self._h, side, lvl, k, ctypes.byref(cnt), ctypes.byref(rows),
+                                                ctypes.byref(cols), ctypes.c_void_p(ranks.ctypes.data),
+                                                ctypes.c_void_p(skel.ctypes.data),
+                                                ctypes.c_void_p(blocks.ctypes.data)))
+                    out["factors"][(side, lvl, k)] = {"ranks": ranks, "skel": skel, "blocks": blocks}
+        pairs, entries = ctypes.c_int64(), ctypes.c_int64()
+        _check(L_.tb_export_cores(self._h, ctypes.byref(pairs), ctypes.byref(entries), None, None, None))
+        offs = np.zeros(pairs.value + 1, dtype=np.int64)
+        dims = np.zeros((pairs.value, 2 * d), dtype=np.int32)
+        core = np.zeros(entries.value, dtype=np.complex128)
+        _check(L_.tb_export_cores(self._h, ctypes.byref(pairs), ctypes.byref(entries), ctypes.c_void_p(offs.ctypes.data),
+                                  ctypes.c_void_p(dims.ctypes.data), ctypes.c_void_p(core.ctypes.data)))
+        out.update(core_offsets=offs, core_dims=dims, core=core)
+        return out
 
     def apply_host_batch(self, fs, us, precision: int | None = None):
         """u_i = K f_i for lists of host arrays (numpy, pinned for overlap), with the

@@ -1890,6 +1890,63 @@ extern "C" tb_status tb_autotune(tb_handle h, int64_t nv, int precision, void *s
     return s;
 }
 
+// ------------------------------------------------------- factor export
+extern "C" tb_status tb_export_factors(tb_handle h, int side, int level, int mode, int64_t *count, int *rows,
+                                       int *cols, int *ranks, int *skel, void *blocks) {
+    if (!h || !count || !rows || !cols) return fail(TB_EINVAL, "handle, count, rows and cols must be non-NULL");
+    if (h->separable) return fail(TB_EUNSUPPORTED, "tb_export_factors: separable handles store per-mode factors");
+    if (side != 0 && side != 1) return fail(TB_EINVAL, "side must be 0 (source) or 1 (target)");
+    if (level < 0 || level > h->Lc) return fail(TB_EINVAL, "level out of range");
+    if (mode < 0 || mode >= h->d) return fail(TB_EINVAL, "mode out of range");
+    const SideLevel &S = side == 0 ? h->src[level] : h->tgt[level];
+    *count = S.count[mode];
+    *rows = S.R[mode];
+    *cols = S.cin[mode];
+    if (!ranks && !skel && !blocks) return TB_OK;
+    if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
+    const int64_t cnt = S.count[mode];
+    if (ranks) TB_CK(cudaMemcpy(ranks, S.rank[mode], (size_t)cnt * sizeof(int), cudaMemcpyDeviceToHost));
+    if (skel) {
+        const size_t w = (size_t)S.R[mode] * sizeof(int), sp = (size_t)S.cap[mode] * sizeof(int);
+        TB_CK(cudaMemcpy2D(skel, w, S.skel[mode], sp, w, (size_t)cnt, cudaMemcpyDeviceToHost));
+    }
+    if (blocks)
+        TB_CK(cudaMemcpy(blocks, S.fac64[mode], (size_t)cnt * S.R[mode] * S.cin[mode] * sizeof(c128),
+                         cudaMemcpyDeviceToHost));
+    return TB_OK;
+}
+
+extern "C" tb_status tb_export_cores(tb_handle h, int64_t *pairs, int64_t *entries, int64_t *offsets, int *dims,
+                                     void *core) {
+    if (!h || !pairs || !entries) return fail(TB_EINVAL, "handle, pairs and entries must be non-NULL");
+    if (h->separable) return fail(TB_EUNSUPPORTED, "tb_export_cores: separable handles store per-mode cores");
+    *pairs = h->P;
+    *entries = h->core_entries;
+    if (!offsets && !dims && !core) return TB_OK;
+    if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
+    if (offsets) TB_CK(cudaMemcpy(offsets, h->core_off, (size_t)(h->P + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (dims) TB_CK(cudaMemcpy(dims, h->core_dims, (size_t)h->P * 2 * h->d * sizeof(int), cudaMemcpyDeviceToHost));
+    if (core) {
+        if (h->core64) {
+            TB_CK(cudaMemcpy(core, h->core64, (size_t)h->core_entries * sizeof(c128), cudaMemcpyDeviceToHost));
+        } else {   // built without complex128: the complex64 cores, widened
+            std::vector<c64> tmp((size_t)h->core_entries);
+            TB_CK(cudaMemcpy(tmp.data(), h->core32, tmp.size() * sizeof(c64), cudaMemcpyDeviceToHost));
+            c128 *o = (c128 *)core;
+            for (size_t i = 0; i < tmp.size(); ++i) o[i] = c128{(double)tmp[i].x, (double)tmp[i].y};
+        }
+    }
+    return TB_OK;
+}
+
+extern "C" tb_status tb_export_order(tb_handle h, int axis, int *perm) {
+    if (!h || !perm) return fail(TB_EINVAL, "handle and perm must be non-NULL");
+    if (axis < 0 || axis >= h->d) return fail(TB_EINVAL, "axis out of range");
+    if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
+    TB_CK(cudaMemcpy(perm, h->perm[axis], (size_t)h->n[axis] * sizeof(int), cudaMemcpyDeviceToHost));
+    return TB_OK;
+}
+
 // ------------------------------------------------- least squares (CGLS)
 namespace {
 

@@ -1,0 +1,236 @@
+"""The GPU apply against the step-by-step oracle (oracle/butterfly.py) on the
+butterfly's own exported factors, and isolated checks of the IDs (Sec. 2.1).
+
+The direct-sum oracle only bounds the apply to the ID tolerance; here the
+CUDA construction's factors, cores and orderings are exported
+(tb_export_factors / _cores / _order) and applied by a plain FP64
+implementation of Alg. 2, so the CUDA apply must match it to rounding:
+complex128 to 1e-12, complex64 to its FP32 rounding, the split-BF16 core to
+its two-term BF16 rounding.  The step-by-step oracle itself is pinned here
+against the mathematics: on the bit-reversed uniform DFT every block is an
+exact rank-C_b DFT block, so the exported butterfly must reproduce the DFT
+identity to rounding, and on the Green's and Radon kernels it must agree with
+the direct sum to the ID tolerance.  The IDs are checked on their own: each
+block is the identity on its skeleton columns (V = [I, R11^-1 R12] Pi^T), it
+reconstructs held-out rows of its unfolding to the tolerance, and its rank is
+within one of a reference column-pivoted QR (scipy) on those rows.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import butterfly as O2
+import paper_2411_03029_gb300 as tb
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+ALL = (1 << tb.PREC_C128) | (1 << tb.PREC_C64) | (1 << tb.PREC_C64_SPLITBF16)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    tb.build.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def rel(a, b):
+    a = np.asarray(a).reshape(-1)
+    b = np.asarray(b).reshape(-1)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def gpu(op, f, prec, adjoint=False):
+    x = f.to(tb.dtype_of(prec)).cuda()
+    y = op.apply_adjoint(x, prec) if adjoint else op.apply(x, prec)
+    return y.cpu().to(torch.complex128).numpy()
+
+
+# rounding bounds of the CUDA apply against the FP64 step-by-step oracle
+ROUND = {tb.PREC_C128: 1e-12, tb.PREC_C64: 2e-6, tb.PREC_C64_SPLITBF16: 5e-5}
+
+
+@pytest.mark.parametrize("d,n,L", [(2, 16, 2), (2, 64, 4), (3, 16, 2)])
+def test_step_oracle_on_the_exact_dft_butterfly(d, n, L):
+    w = W.Workload(name="f", kind=W.FOURIER, d=d, n=n, tol=1e-8, nv=2, precision=W.C128, bound=1e-12,
+                   rhs_seeds=(0, 1), samples=0, order=W.ORDER_BITREV, L=L)
+    op = tb.from_workload(w, separable=0, precisions=ALL)
+    bf = op.export()
+    f = W.rhs(w)
+    u = O2.apply(bf, f.numpy())
+    v = O2.apply_adjoint(bf, f.numpy())
+    assert rel(u, oracle.fourier_fft(f.numpy(), d)) < 1e-12
+    assert rel(v, oracle.fourier_fft_adjoint(f.numpy(), d)) < 1e-12
+    for prec, bound in ROUND.items():
+        assert rel(gpu(op, f, prec), u) < bound, prec
+        assert rel(gpu(op, f, prec, adjoint=True), v) < bound, prec
+    op.close()
+
+
+CASES = {
+    "helmholtz3d": W.small("helmholtz3d_n64", 16, nv=3, L=2),
+    "radon2d": W.small("radon2d_n256", 64, nv=3, L=4),
+    "helmholtz3d_n32_bf16": W.small("helmholtz3d_n256", 32, nv=16, L=2, params=(2 * np.pi * 8,)),
+}
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_gpu_apply_matches_step_oracle_to_rounding(name):
+    w = CASES[name]
+    op = tb.from_workload(w, precisions=ALL)
+    bf = op.export()
+    f = W.rhs(w)
+    u = O2.apply(bf, f.numpy())
+    v = O2.apply_adjoint(bf, f.numpy())
+    # the step oracle is the butterfly: within the ID tolerance of the direct sum
+    rows = W.sample_targets(w, 256, seed=4096)
+    assert rel(u.reshape(-1, w.nv)[rows], oracle.workload_apply(w, f, rows)) < 10 * w.tol
+    assert rel(v.reshape(-1, w.nv)[rows], oracle.workload_apply_adjoint(w, f, rows)) < 10 * w.tol
+    for prec, bound in ROUND.items():
+        assert rel(gpu(op, f, prec), u) < bound, prec
+        assert rel(gpu(op, f, prec, adjoint=True), v) < bound, prec
+    op.close()
+
+
+def test_cores_are_the_kernel_at_the_skeleton_points():
+    w = W.small("radon2d_n256", 32, nv=1, L=2)
+    op = tb.from_workload(w, precisions=1 << tb.PREC_C128)
+    bf = op.export()
+    xs, ys = W.grids(w)
+
+    def kern(i, j):
+        X = np.array([[xs[k][i[k]] for k in range(w.d)]])
+        Y = np.array([[ys[k][j[k]] for k in range(w.d)]])
+        return oracle.kernel_matrix(w.kind, w.params, X, Y)[0, 0]
+
+    ref = O2.cores_from_kernel(bf, kern)
+    assert np.max(np.abs(ref - bf["core"])) < 1e-12 * np.max(np.abs(ref))
+    op.close()
+
+
+# ------------------------------------------------------------------- the IDs
+def _flat_unflat(flat, l, d):
+    return [(flat >> (l * (d - 1 - k))) & ((1 << l) - 1) for k in range(d)]
+
+
+def _candidates(bf, side, l, k, j, S, T, q):
+    """Grid indices along mode k of a block's candidate columns (-1 for padding)."""
+    d, Lc = bf["d"], bf["Lc"]
+    F = bf["factors"][(side, l, k)]
+    cols = F["blocks"].shape[2]
+    if l == 0:
+        Sk = _flat_unflat(S, Lc, d)[k]
+        w = bf["n"][k] >> Lc
+        base = Sk * w + q * bf["cb"][k]
+        return bf["perm"][k][base:base + cols].astype(np.int64)
+    Fp = bf["factors"][(side, l - 1, k)]
+    Rp = Fp["blocks"].shape[1]
+    pT = 0
+    for i in _flat_unflat(T, l, d):
+        pT = (pT << (l - 1)) | (i >> 1)
+    jc = ((S << (d * (l - 1))) + pT) * (1 << (Lc - l + 1)) + 2 * q
+    cand = np.full(cols, -1, dtype=np.int64)
+    for c in range(2):
+        r = Fp["ranks"][jc + c]
+        cand[c * Rp:c * Rp + r] = Fp["skel"][jc + c][:r]
+    return cand
+
+
+def _blocks(bf):
+    d, Lc = bf["d"], bf["Lc"]
+    for (side, l, k), F in bf["factors"].items():
+        nF, nT, nq = 1 << (d * Lc), 1 << (d * l), 1 << (Lc - l)
+        for S in range(nF):
+            for T in range(nT):
+                for q in range(nq):
+                    yield side, l, k, ((S * nT) + T) * nq + q, S, T, q
+
+
+def test_every_id_is_the_identity_on_its_skeleton_columns():
+    w = W.small("helmholtz3d_n64", 16, nv=1, L=2)
+    op = tb.from_workload(w, precisions=1 << tb.PREC_C128)
+    bf = op.export()
+    checked = 0
+    for side, l, k, j, S, T, q in _blocks(bf):
+        F = bf["factors"][(side, l, k)]
+        r = F["ranks"][j]
+        cand = _candidates(bf, side, l, k, j, S, T, q)
+        sk = F["skel"][j][:r]
+        pos = [int(np.flatnonzero(cand == g)[0]) for g in sk]     # every skeleton is a candidate
+        A = F["blocks"][j][:r]
+        assert np.allclose(A[:, pos], np.eye(r), atol=1e-12), (side, l, k, j)
+        assert np.all(A[:, cand < 0] == 0)                         # padding columns are zero
+        checked += 1
+    assert checked > 100
+    op.close()
+
+
+def _heldout_rows(bf, w, side, l, k, S, T, m, rng):
+    """m random rows of the unfolding that a block's ID compresses, as point
+    coordinates: (other-side points, own-side points with mode k left free)."""
+    d, Lc = bf["d"], bf["Lc"]
+    xs, ys = W.grids(w)
+    own, oth = (ys, xs) if side == 0 else (xs, ys)
+    Tn, Sn = _flat_unflat(T, l, d), _flat_unflat(S, Lc, d)
+    P_oth = np.zeros((m, d))
+    P_own = np.zeros((m, d))
+    for i in range(d):
+        wt = bf["n"][i] >> l                       # other-side node at level l
+        pos = Tn[i] * wt + rng.integers(0, wt, m)
+        P_oth[:, i] = oth[i][bf["perm"][i][pos]]
+        ws = bf["n"][i] >> Lc                      # own-side mid-level node (mode k replaced by the candidates)
+        pos = Sn[i] * ws + rng.integers(0, ws, m)
+        P_own[:, i] = own[i][bf["perm"][i][pos]]
+    return P_oth, P_own, own
+
+
+def _id_matrix(w, side, P_oth, P_own, own, k, idx):
+    cols = []
+    for g in idx:
+        Q = P_own.copy()
+        Q[:, k] = own[k][g]
+        X, Y = (P_oth, Q) if side == 0 else (Q, P_oth)
+        cols.append(oracle.kernel_pairs(w.kind, w.params, X, Y))
+    return np.stack(cols, axis=1)
+
+
+def test_ids_reconstruct_heldout_rows_and_match_pivoted_qr_ranks():
+    sla = pytest.importorskip("scipy.linalg")
+    w = W.small("radon2d_n256", 64, nv=1, L=4)
+    op = tb.from_workload(w, precisions=1 << tb.PREC_C128)
+    bf = op.export()
+    rng = np.random.default_rng(2024)
+    blocks = list(_blocks(bf))
+    pick = rng.choice(len(blocks), size=60, replace=False)
+    num = den = 0.0
+    worst, rank_off = 0.0, []
+    for b in pick:
+        side, l, k, j, S, T, q = blocks[b]
+        F = bf["factors"][(side, l, k)]
+        r = int(F["ranks"][j])
+        cand = _candidates(bf, side, l, k, j, S, T, q)
+        live = cand >= 0
+        P_oth, P_own, own = _heldout_rows(bf, w, side, l, k, S, T, 384, rng)
+        A = _id_matrix(w, side, P_oth, P_own, own, k, cand[live])
+        Ask = _id_matrix(w, side, P_oth, P_own, own, k, F["skel"][j][:r])
+        E = A - Ask @ F["blocks"][j][:r][:, live]
+        num += np.linalg.norm(E) ** 2
+        den += np.linalg.norm(A) ** 2
+        worst = max(worst, np.linalg.norm(E) / np.linalg.norm(A))
+        # reference rank: smallest r with ||R22||_F <= eps ||A||_F after pivoted QR
+        R = sla.qr(A, pivoting=True, mode="r")[0]
+        tail = np.sqrt(np.cumsum((np.abs(R) ** 2).sum(axis=1)[::-1])[::-1])
+        nA = np.linalg.norm(A)
+        rref = next((i for i in range(1, A.shape[1] + 1) if (tail[i] if i < len(tail) else 0.0) <= w.tol * nA),
+                    A.shape[1])
+        rank_off.append(r - rref)
+    agg = np.sqrt(num / den)
+    print(f"held-out ID error: aggregate {agg:.2e}, worst block {worst:.2e}; rank - reference: "
+          f"{np.bincount(np.array(rank_off) + 8)}")
+    assert agg <= 10 * w.tol
+    assert worst <= 100 * w.tol
+    off = np.abs(np.array(rank_off))
+    assert np.mean(off <= 1) >= 0.9 and off.max() <= 3
+    op.close()

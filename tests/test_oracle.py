@@ -238,3 +238,11 @@ def test_workload_definitions():
     assert np.array_equal(f[..., 2].numpy(), W.complex_gaussian((8, 8, 8), 2).numpy())
     b = W.smooth_bumps(W.WORKLOADS["radon2d_n256"])
     assert b.shape == (256, 256, 1)
+
+
+def test_kernel_pairs_is_the_diagonal_of_kernel_matrix():
+    rng = np.random.default_rng(8)
+    X, Y = rng.random((7, 3)), rng.random((7, 3)) + 2.0
+    for kind, params in ((W.FOURIER, ()), (W.HELMHOLTZ, (5.0, 0.3)), (W.RADON, (0.1, 0.05))):
+        K = oracle.kernel_matrix(kind, params, X, Y)
+        assert np.allclose(oracle.kernel_pairs(kind, params, X, Y), np.diag(K), rtol=0, atol=1e-14)
