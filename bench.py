@@ -53,6 +53,8 @@ def parse():
                         "3-D Helmholtz configuration when they apply; else the live oracle, capped)")
     p.add_argument("--profile-only", action="store_true", help="eager applies only (for ncu)")
     p.add_argument("--n", type=int, default=None, help="points per axis of a reduced-size copy (profiling)")
+    p.add_argument("--level-schedule", type=int, default=0,
+                   help="non-separable handles: tb_options.level_schedule (0 rule, 1 per-mode, 2 fused)")
     p.add_argument("--sep-schedule", type=int, default=0,
                    help="separable handles: tb_options.sep_schedule (0 rule; the tuner may replace it)")
     return p.parse_args()
@@ -311,7 +313,7 @@ def main():
     prec = args.precision if args.precision is not None else w.precision
     mask = (1 << prec) | ((1 << tb.PREC_C128) if not args.no_fp64 else 0)
     op = tb.from_workload(w, precisions=mask, use_graphs=not args.profile_only, precision=prec,
-                          sep_schedule=args.sep_schedule)
+                          sep_schedule=args.sep_schedule, level_schedule=args.level_schedule)
     info = op.info()
     nv = w.nv
     tune_s = None

@@ -117,6 +117,12 @@ typedef struct {
                               5 = as 3 with scalar FMAs, one fiber per thread and the
                                   next fiber's loads in flight,
                               6 = as 3 with one fiber per thread (4 resident blocks per SM) */
+    int level_schedule;    /* non-separable level passes (Alg. 2 steps 1 and 3), complex64:
+                              0 = built-in rule (= 2 where it applies: d <= 3),
+                              1 = d launches per pass, one per mode product,
+                              2 = one fused persistent launch per pass (the mode products
+                                  of a unit back to back, intermediates in a per-block
+                                  scratch); complex128 always uses 1 */
 } tb_options;
 
 typedef struct tb_plan *tb_handle;

@@ -131,6 +131,7 @@ tb_status tb_options_default(tb_options *o) {
     o->seed = 0x5eed;
     o->autotune = 0;
     o->sep_schedule = 0;
+    o->level_schedule = 0;
     return TB_OK;
 }
 
@@ -887,6 +888,7 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     if (L % 2 != 0 || L < 0 || L >= TB_MAX_LEVELS || (nmin >> L) < 1)
         return fail(TB_EINVAL, "L must be even with n_k / 2^L >= 1");
     if (opt.sep_schedule < 0 || opt.sep_schedule > 6) return fail(TB_EINVAL, "sep_schedule must be in [0, 6]");
+    if (opt.level_schedule < 0 || opt.level_schedule > 2) return fail(TB_EINVAL, "level_schedule must be in [0, 2]");
     int dev = opt.device;
     if (dev < 0) {
         if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "no CUDA device"); }
@@ -915,6 +917,7 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     h->use_graphs = opt.use_graphs;
     h->autotune = opt.autotune;
     h->sep_choice = opt.sep_schedule;
+    h->level_choice = opt.level_schedule;
     h->proxy_rows = opt.proxy_rows;
     h->rank_max = opt.rank_max;
     h->seed = opt.seed;
@@ -1195,6 +1198,217 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
     return TB_OK;
 }
 
+// Complex multiply-adds per RHS of a chain X (dims m) -> Y (dims o) applied
+// in the mode order `ord`.
+double chain_cmacs_order(int d, const int *m, const int *o, const int *ord) {
+    int cur[TB_MAX_D];
+    for (int k = 0; k < d; ++k) cur[k] = m[k];
+    double f = 0.0;
+    for (int i = 0; i < d; ++i) {
+        const int k = ord[i];
+        double t = (double)m[k] * o[k];
+        for (int j = 0; j < d; ++j)
+            if (j != k) t *= cur[j];
+        f += t;
+        cur[k] = o[k];
+    }
+    return f;
+}
+
+// The mode order with the fewest multiply-adds (ties: lexicographically first).
+double best_order(int d, const int *m, const int *o, int *ord) {
+    std::vector<int> p((size_t)d);
+    for (int k = 0; k < d; ++k) p[(size_t)k] = k;
+    double best = -1.0;
+    do {
+        const double f = chain_cmacs_order(d, m, o, p.data());
+        if (best < 0.0 || f < best) {
+            best = f;
+            for (int k = 0; k < d; ++k) ord[k] = p[(size_t)k];
+        }
+    } while (std::next_permutation(p.begin(), p.end()));
+    return best;
+}
+
+// Input / output lengths of each mode of one unit of a level pass.
+void pass_dims(const tb_plan *h, Pass pass, int side, int l, int *m, int *o) {
+    const SideLevel *S = side == 0 ? h->src : h->tgt;
+    for (int k = 0; k < h->d; ++k) {
+        switch (pass) {
+            case Pass::LeafIn: m[k] = (int)h->cb[k]; o[k] = S[0].R[k]; break;
+            case Pass::LeafOut: m[k] = S[0].R[k]; o[k] = (int)h->cb[k]; break;
+            case Pass::Split: m[k] = 2 * S[l - 1].R[k]; o[k] = S[l].R[k]; break;
+            case Pass::Gather: m[k] = S[l].R[k]; o[k] = 2 * S[l - 1].R[k]; break;
+        }
+    }
+}
+
+// Whether a level pass runs fused: tb_options.level_schedule, then the tuner's
+// per-pass choice (the faster of the two forms), then the built-in rule
+// (per-mode launches).
+bool level_fused_wanted(const tb_plan *h, Pass pass, int side, int l) {
+    if (h->level_choice == 1) return false;
+    if (h->level_choice == 2) return true;
+    const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
+    return h->ltune[side][(int)pass][leaf ? 0 : l].mode == 2;
+}
+
+// One level pass as a single fused persistent launch (k_level, complex64),
+// its intermediates in `scratch` (scratch_bytes long).  done = false (and
+// nothing launched) when the pass does not fit the fused kernel: d > 3, too
+// little scratch or shared memory.  dry = true only plans.
+tb_status level_pass_fused(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out,
+                           int64_t nv, cudaStream_t st, void *scratch, size_t scratch_bytes, bool &done,
+                           bool dry = false, int vc_set = 0, int cps_set = 0, int obmax_set = 0) {
+    done = false;
+    const int d = h->d, Lc = h->Lc;
+    if (d > 3 || (1 << d) > level_max_children()) return TB_OK;
+    const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
+    LevelArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.d = d;
+    a.Lc = Lc;
+    a.pass = (int)pass;
+    a.nv = nv;
+    a.nF = ipow2(d * Lc);
+    a.trans = (pass == Pass::LeafOut || pass == Pass::Gather) ? 1 : 0;
+    a.conj = conj ? 1 : 0;
+    int m[TB_MAX_D], o[TB_MAX_D];
+    pass_dims(h, pass, side, l, m, o);
+    const SideLevel *S = side == 0 ? h->src : h->tgt;
+    for (int k = 0; k < d; ++k) {
+        a.m[k] = m[k];
+        a.o[k] = o[k];
+        a.cb[k] = (int)h->cb[k];
+        a.nmid[k] = h->n[k] >> Lc;
+        a.perm[k] = h->perm[k];
+        if (!leaf) a.Rp[k] = S[l - 1].R[k];
+    }
+    int64_t gs = 1;
+    for (int k = d - 1; k >= 0; --k) {
+        a.user.gstride[k] = gs;
+        gs *= h->n[k];
+    }
+    switch (pass) {
+        case Pass::LeafIn:
+            a.user.p = (cx<float> *)in;
+            a.lout = tilebuf<float>(h, side, 0, out);
+            a.fac = facref<float>(h, side, 0);
+            break;
+        case Pass::LeafOut:
+            a.user.p = (cx<float> *)out;
+            a.lin = tilebuf<float>(h, side, 0, (void *)in);
+            a.fac = facref<float>(h, side, 0);
+            break;
+        case Pass::Split:
+            a.lin = tilebuf<float>(h, side, l - 1, (void *)in);
+            a.lout = tilebuf<float>(h, side, l, out);
+            a.fac = facref<float>(h, side, l);
+            break;
+        case Pass::Gather:
+            a.lin = tilebuf<float>(h, side, l, (void *)in);
+            a.lout = tilebuf<float>(h, side, l - 1, out);
+            a.fac = facref<float>(h, side, l);
+            break;
+    }
+    a.lvl = leaf ? 0 : l;
+    a.lgs = Lc - a.lvl;
+    best_order(d, m, o, a.order);
+    const tb::LevelTune &tn = h->ltune[side][(int)pass][leaf ? 0 : l];
+    // output rows per register chunk, one value for the launch: the even value
+    // in [4, 16] with the fewest padded multiply-adds (ties: fewer chunks)
+    int OB = obmax_set ? obmax_set : tn.obmax;
+    if (!level_ob_valid(OB)) {
+        double best = -1.0;
+        int cur[TB_MAX_D];
+        double stepc[TB_MAX_D];
+        for (int k = 0; k < d; ++k) cur[k] = m[k];
+        for (int i = 0; i < d; ++i) {
+            const int k = a.order[i];
+            double t = (double)m[k];
+            for (int j = 0; j < d; ++j)
+                if (j != k) t *= cur[j];
+            stepc[k] = t;   // multiply-adds per output row of mode k
+            cur[k] = o[k];
+        }
+        for (int ob = 12; ob >= 4; ob -= 2) {   // 14 and 16 spill registers: tuner only
+            double c = 0.0;
+            for (int k = 0; k < d; ++k) c += stepc[k] * ((o[k] + ob - 1) / ob * ob);
+            if (best < 0.0 || c < best * (1.0 - 1e-9)) {
+                best = c;
+                OB = ob;
+            }
+        }
+    }
+    for (int k = 0; k < d; ++k) a.lda[k] = (o[k] + OB - 1) / OB * OB;
+    int off = 0;
+    for (int k = 0; k < d; ++k) {
+        a.fac_off[k] = off;
+        off += (3 * m[k] * a.lda[k] + 3) / 4 * 4;   // planes start on 16-byte boundaries
+    }
+    a.fac_floats = off;
+    for (int i = 0; i < d; ++i) a.ob[i] = OB;
+    int64_t gtab = 0;
+    for (int k = 0; k < d; ++k) gtab += h->cb[k];
+    // shared memory: factors, tree-order tables, two intermediate buffers and
+    // (Gather) the combined parent tile, for vc right-hand sides per item
+    int64_t inter[2] = {0, 0};   // entries per RHS of the even / odd step outputs
+    {
+        int cur[TB_MAX_D];
+        for (int k = 0; k < d; ++k) cur[k] = m[k];
+        for (int i = 0; i + 1 < d; ++i) {
+            cur[a.order[i]] = o[a.order[i]];
+            int64_t t = 1;
+            for (int k = 0; k < d; ++k) t *= cur[k];
+            inter[i & 1] = std::max(inter[i & 1], t);
+        }
+    }
+    int64_t accn = 0;
+    if (pass == Pass::Gather) {
+        accn = 1;
+        for (int k = 0; k < d; ++k) accn *= o[k];
+    }
+    auto up16 = [](size_t b) { return (b + 15) / 16 * 16; };
+    const size_t gstr_off = up16((size_t)a.fac_floats * sizeof(float) + (leaf ? (size_t)gtab * sizeof(int) : 0));
+    const size_t fixed = up16(gstr_off + (leaf ? (size_t)gtab * sizeof(int64_t) : 0));
+    a.off_gstr = gstr_off;
+    for (int k = 0; k < d; ++k) a.lcb[k] = ilog2(h->cb[k]);
+    int64_t inn = 1;
+    for (int k = 0; k < d; ++k) inn *= m[k];
+    auto smem_for = [&](int v) {
+        return fixed + up16((size_t)inn * v * sizeof(float2)) + up16((size_t)inter[0] * v * sizeof(float2)) +
+               up16((size_t)inter[1] * v * sizeof(float2)) + up16((size_t)accn * v * sizeof(float2));
+    };
+    // two resident blocks per SM by default (the static shared arrays take ~1 KB each)
+    const size_t budget = std::min<size_t>(g_smem_optin, 110 * 1024);
+    int vc = vc_set ? vc_set : tn.vc;
+    if (vc <= 0) {
+        vc = 4;
+        while (vc > 1 && smem_for(vc) > budget) vc /= 2;
+    }
+    vc = (int)std::max<int64_t>(1, std::min<int64_t>(vc, nv));
+    while (vc & (vc - 1)) --vc;   // a power of two
+    a.smem = smem_for(vc);
+    if (a.smem > g_smem_optin) return TB_OK;
+    a.off_in = fixed;
+    a.off_s0 = a.off_in + up16((size_t)inn * vc * sizeof(float2));
+    a.off_s1 = a.off_s0 + up16((size_t)inter[0] * vc * sizeof(float2));
+    a.off_acc = a.off_s1 + up16((size_t)inter[1] * vc * sizeof(float2));
+    a.vc = vc;
+    a.lvc = ilog2(vc);
+    a.nq = (int)((nv + vc - 1) / vc);
+    const int64_t nunits = leaf ? h->P : (h->P >> d);
+    a.nitems = nunits * a.nq;
+    const int cps = cps_set ? cps_set : (tn.cps ? tn.cps : 2);
+    const int64_t blocks = std::min<int64_t>(a.nitems, (int64_t)cps * g_num_sms);
+    (void)scratch;
+    (void)scratch_bytes;
+    done = true;
+    if (dry) return TB_OK;
+    TB_CK(launch_level(a, OB, (int)blocks, st));
+    return TB_OK;
+}
+
 template <class R>
 const cx<R> *coreptr(const tb_plan *h);
 template <>
@@ -1271,6 +1485,12 @@ tb_status core_pass(const tb_plan *h, bool adjoint, const void *in, void *out, i
     a.nvc = c;
     a.smem = (size_t)(tmax * c * es);
     if (a.smem > g_smem_optin) return fail(TB_EUNSUPPORTED, "core block exceeds shared memory");
+    if constexpr (std::is_same<R, float>::value) {
+        if (!adjoint && nv == 1 && h->core_rows) {
+            TB_CK(launch_core_rows<float>(a, st));
+            return TB_OK;
+        }
+    }
     TB_CK(launch_core_dense<R>(adjoint, a, st));
     return TB_OK;
 }
@@ -1304,18 +1524,17 @@ void pass_cost(const tb_plan *h, Pass pass, int side, int l, int64_t nv, size_t 
         case Pass::LeafIn:
         case Pass::LeafOut:
             bytes = N * nv * (int64_t)es + tensor(0) + facb(0);
-            for (int k = 0; k < d; ++k) { m[k] = (int)h->cb[k]; o[k] = S[0].R[k]; }
-            if (pass == Pass::LeafOut) std::swap(m, o);
-            flops = (double)h->P * nv * chain_flops(d, m, o);
             break;
         case Pass::Split:
         case Pass::Gather:
             bytes = tensor(l - 1) + tensor(l) + facb(l);
-            for (int k = 0; k < d; ++k) { m[k] = 2 * S[l - 1].R[k]; o[k] = S[l].R[k]; }
-            if (pass == Pass::Gather) std::swap(m, o);
-            flops = (double)h->P * nv * chain_flops(d, m, o);
             break;
     }
+    // algorithmic flops: 8 per complex multiply-add of the chain in its
+    // fewest-multiply mode order (the products of a chain commute)
+    pass_dims(h, pass, side, l, m, o);
+    int ord[TB_MAX_D];
+    flops = 8.0 * (double)h->P * nv * best_order(d, m, o, ord);
 }
 
 template <class R>
@@ -1557,14 +1776,16 @@ tb_status run_sep(tb_plan *h, bool adjoint, const void *in, void *out, int64_t n
 // keeps them.
 template <class R>
 tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st, bool prof,
-                    int precision, void *const *bufs = nullptr) {
+                    int precision, void *const *bufs = nullptr, size_t t0_bytes = 0) {
     void *B[2] = {h->ws.buf[0], h->ws.buf[1]};
     void *T[2] = {h->ws.mbuf[0], h->ws.mbuf[1]};
+    size_t T0bytes = h->ws.mbytes[0];
     if (bufs) {
         B[0] = bufs[0];
         B[1] = bufs[1];
         T[0] = bufs[2];
         T[1] = bufs[3];
+        T0bytes = t0_bytes;
     }
     if (h->separable) return run_sep<R>(h, adjoint, in, out, nv, st, prof, B);
     const int Lc = h->Lc, d = h->d;
@@ -1589,6 +1810,15 @@ tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t
         int64_t bytes = 0;
         double flops = 0;
         if (prof) pass_cost(h, p, side, l, nv, es, bytes, flops);
+        if (std::is_same<R, float>::value && h->level_choice != 1 && level_fused_wanted(h, p, side, l)) {
+            bool ok = false;
+            TB_TRY(level_pass_fused(h, p, adjoint, side, l, i, o, nv, st, T[0], T0bytes, ok, true));
+            if (ok)
+                return timed(name, l, bytes, flops, 1, [&] {
+                    bool done = false;
+                    return level_pass_fused(h, p, adjoint, side, l, i, o, nv, st, T[0], T0bytes, done);
+                });
+        }
         return timed(name, l, bytes, flops, d,
                      [&] { return level_pass<R>(h, p, adjoint, side, l, i, o, nv, st, T); });
     };
@@ -1714,6 +1944,56 @@ tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, cons
     } else {
         void *B[2] = {h->ws.buf[0], h->ws.buf[1]};
         void *T[2] = {h->ws.mbuf[0], h->ws.mbuf[1]};
+        // fused level passes (complex64): RHS per work item, blocks per SM and
+        // output rows per register chunk; every candidate accumulates each
+        // output in the same order, so the choice does not change results
+        if (std::is_same<R, float>::value && h->level_choice != 1) {
+            const Pass fpasses[4] = {Pass::LeafIn, Pass::Split, Pass::Gather, Pass::LeafOut};
+            for (int side = 0; side < 2 && status == TB_OK; ++side)
+                for (Pass p : fpasses) {
+                    const bool leaf = p == Pass::LeafIn || p == Pass::LeafOut;
+                    for (int l = leaf ? 0 : 1; l <= (leaf ? 0 : h->Lc) && status == TB_OK; ++l) {
+                        const void *in = p == Pass::LeafIn ? uin : B[0];
+                        void *out = p == Pass::LeafOut ? uout : (p == Pass::LeafIn ? B[0] : B[1]);
+                        tb::LevelTune best;
+                        h->ltune[side][(int)p][l] = best;   // candidates start from the built-in rule
+                        float tbest = 3.0e38f;
+                        for (int vc : {1, 2, 4})
+                            for (int cps : {2, 3, 4})
+                                for (int ob : {0, 8}) {
+                                    bool ok = false;
+                                    status = level_pass_fused(h, p, false, side, l, in, out, nv, st, T[0],
+                                                              h->ws.mbytes[0], ok, true, vc, cps, ob);
+                                    if (status != TB_OK || !ok) continue;
+                                    float t = 0.f;
+                                    status = time_it(
+                                        [&] {
+                                            bool done = false;
+                                            return level_pass_fused(h, p, false, side, l, in, out, nv, st, T[0],
+                                                                    h->ws.mbytes[0], done, false, vc, cps, ob);
+                                        },
+                                        t);
+                                    if (status != TB_OK) break;
+                                    if (t < tbest) {
+                                        tbest = t;
+                                        best.mode = 2;
+                                        best.vc = vc;
+                                        best.cps = cps;
+                                        best.obmax = ob;
+                                    }
+                                }
+                        if (best.mode == 2 && h->level_choice == 0) {
+                            // against the per-mode launches of the same pass (their shapes
+                            // as tuned below are not known yet: the built-in ones)
+                            float tmode = 3.0e38f;
+                            status = time_it(
+                                [&] { return level_pass<R>(h, p, false, side, l, in, out, nv, st, T); }, tmode);
+                            if (status == TB_OK && tmode <= tbest) best.mode = 1;
+                        }
+                        h->ltune[side][(int)p][l] = best;
+                    }
+                }
+        }
         const int ri = std::is_same<R, double>::value ? 1 : 0;
         const Pass passes[4] = {Pass::LeafIn, Pass::Split, Pass::Gather, Pass::LeafOut};
         const int waves[3] = {8, 32, 128};
@@ -2137,8 +2417,8 @@ extern "C" tb_status tb_apply_noalloc(tb_handle h, const void *f, void *u, int64
     unsigned char *sb = (unsigned char *)base;
     void *bufs[4] = {sb, sb + half, sb + 2 * half, sb + 2 * half + mreg[0]};
     cudaStream_t st = (cudaStream_t)stream;
-    if (precision == TB_PREC_C128) return run_chain<double>(h, false, f, u, nv, st, false, precision, bufs);
-    return run_chain<float>(h, false, f, u, nv, st, false, precision, bufs);
+    if (precision == TB_PREC_C128) return run_chain<double>(h, false, f, u, nv, st, false, precision, bufs, mreg[0]);
+    return run_chain<float>(h, false, f, u, nv, st, false, precision, bufs, mreg[0]);
 }
 
 extern "C" tb_status tb_apply_host(tb_handle h, const void *f, void *u, int64_t nv, int precision) {

@@ -298,6 +298,97 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core_dense(const CoreApplyArgs
     }
 }
 
+// Forward core for one right-hand side, complex64: G_{t,s}[a] = sum_b C[a][b] F_{t,s}[b].
+// A warp takes 32 core rows at a time; lane l takes columns l, l + 32, .. and
+// accumulates all 32 rows, reading each row
+// coalesced (32 consecutive entries per load, 32 independent loads in flight
+// per lane); a transposed butterfly reduction (31 exchanges per component for
+// the 32 rows) then leaves row r0 + l's sum in lane l.  Columns of a row are
+// summed in the same order for every row (lane-strided partial sums, then the
+// butterfly): deterministic.
+template <class R>
+__global__ void __launch_bounds__(CORE_THREADS) k_core_rows(const CoreApplyArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cx<R> *Xc = reinterpret_cast<cx<R> *>(smraw);
+    const int d = a.d;
+    const int64_t p = blockIdx.x;
+    int rt[MAXD], rs[MAXD];
+    int Mt = 1, Ms = 1;
+    for (int k = 0; k < d; ++k) {
+        rt[k] = a.dims[p * 2 * d + k];
+        rs[k] = a.dims[p * 2 * d + d + k];
+        Mt *= rt[k];
+        Ms *= rs[k];
+    }
+    const cx<R> *C = a.core + a.off[p];
+    const cx<R> *src = a.in.p + p * a.in.tsize * a.nv;
+    cx<R> *dst = a.out.p + p * a.out.tsize * a.nv;
+    for (int b = threadIdx.x; b < Ms; b += blockDim.x) {
+        int q = b, pos = 0, stride = 1;
+        for (int k = d - 1; k >= 0; --k) {
+            pos += (q % rs[k]) * stride;
+            q /= rs[k];
+            stride *= a.in.R[k];
+        }
+        Xc[b] = src[(int64_t)pos * a.nv];
+    }
+    for (int e = threadIdx.x; e < a.out.tsize; e += blockDim.x) dst[(int64_t)e * a.nv] = {R(0), R(0)};
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nk = (Ms + 31) >> 5;
+    for (int r0 = warp * 32; r0 < Mt; r0 += nw * 32) {
+        cx<R> acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = {R(0), R(0)};
+        const int nr = Mt - r0 < 32 ? Mt - r0 : 32;
+#pragma unroll 1
+        for (int k = 0; k < nk; ++k) {
+            const int b = lane + 32 * k;
+            const bool live = b < Ms;
+            const cx<R> *col = C + (int64_t)r0 * Ms + b;
+            const cx<R> xk = live ? Xc[b] : cx<R>{R(0), R(0)};
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const cx<R> c = (live && j < nr) ? col[(int64_t)j * Ms] : cx<R>{R(0), R(0)};
+                cmac(acc[j], c, xk);
+            }
+        }
+        // transposed reduction: after the step with offset o, lane l keeps the
+        // partial sums of the rows whose bit o equals lane bit o
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int j = 0; j < o; ++j) {
+                const cx<R> send = up ? acc[j] : acc[j + o];
+                const cx<R> keep = up ? acc[j + o] : acc[j];
+                cx<R> got;
+                got.x = __shfl_xor_sync(0xffffffffu, send.x, o);
+                got.y = __shfl_xor_sync(0xffffffffu, send.y, o);
+                acc[j] = {keep.x + got.x, keep.y + got.y};
+            }
+        }
+        if (lane < nr) {
+            int q = r0 + lane, pos = 0, stride = 1;
+            for (int k = d - 1; k >= 0; --k) {
+                pos += (q % rt[k]) * stride;
+                q /= rt[k];
+                stride *= a.out.R[k];
+            }
+            dst[(int64_t)pos * a.nv] = acc[0];
+        }
+    }
+}
+
+template <class R>
+cudaError_t launch_core_rows(const CoreApplyArgs<R> &a, cudaStream_t st) {
+    cudaError_t e = set_smem_once((const void *)k_core_rows<R>, a.smem);
+    if (e != cudaSuccess) return e;
+    k_core_rows<R><<<(unsigned)a.P, CORE_THREADS, a.smem, st>>>(a);
+    return cudaGetLastError();
+}
+template cudaError_t launch_core_rows<float>(const CoreApplyArgs<float> &, cudaStream_t);
+
 template <class R>
 cudaError_t launch_core_dense(bool adjoint, const CoreApplyArgs<R> &a, cudaStream_t st) {
     const int64_t nchunks = (a.nv + a.nvc - 1) / a.nvc;

@@ -150,6 +150,39 @@ template <class R>
 cudaError_t launch_mode(int in_kind, int out_kind, int ob, const ModeArgs<R> &a, cudaStream_t st);
 int mode_cols_per_block();
 
+// A whole level pass (all d mode products) in one persistent launch
+// (k_level in tb_level.cu), complex64.  Work item = (unit or group, chunk of
+// vc right-hand sides); the intermediates stay in shared memory.
+struct LevelArgs {
+    int d, Lc, pass, lvl, lgs;     // pass: 0 LeafIn, 1 Split, 2 Gather, 3 LeafOut
+    int conj, trans;               // factors applied as op(A) = A or A^T, conjugated or not
+    int order[MAXD];               // mode of step i
+    int ob[MAXD];                  // output rows per register chunk of step i (even, 4 .. 16)
+    int m[MAXD], o[MAXD];          // input / output length of each mode for one unit
+    int lda[MAXD];                 // staged factor row length of mode k (o_k padded to its chunks)
+    int fac_off[MAXD];             // float offset of mode k's staged factor (3 planes of m_k x lda_k)
+    int fac_floats;                // floats of all staged factors
+    int vc, lvc, nq;               // RHS per item (a power of two, lvc = log2), chunks per unit
+    int lcb[MAXD];                 // log2 C_b per mode (leaf passes)
+    int64_t nv, nF, nitems;
+    int cb[MAXD];
+    int64_t nmid[MAXD];
+    const int *perm[MAXD];
+    int Rp[MAXD];                  // parent tile dims (Split input, Gather output)
+    FacRef<float> fac;
+    TileBuf<float> lin, lout;
+    UserArr<float> user;
+    size_t off_gstr;               // byte offset of the leaf tables of grid offsets (int64)
+    size_t off_in, off_s0, off_s1, off_acc;   // byte offsets in shared memory of the staged
+                                      // step-0 input, the two intermediate buffers and
+                                      // (Gather) the combined parent tile
+    size_t smem;
+};
+cudaError_t launch_level(const LevelArgs &a, int ob, int blocks, cudaStream_t st);
+bool level_ob_valid(int ob);
+int level_threads();
+int level_max_children();
+
 template <class R>
 struct CoreApplyArgs {
     int d;
@@ -391,6 +424,9 @@ template <class R>
 cudaError_t launch_core_dense(bool adjoint, const CoreApplyArgs<R> &a, cudaStream_t st);
 template <class R>
 cudaError_t launch_core_kron(bool adjoint, const CoreApplyArgs<R> &a, cudaStream_t st);
+// Forward core for one RHS, complex64, 32 rows per warp (k_core_rows).
+template <class R>
+cudaError_t launch_core_rows(const CoreApplyArgs<R> &a, cudaStream_t st);
 
 // Shared-memory plan of a mode-product chain: input dims m, output dims o.
 struct ChainSmem {

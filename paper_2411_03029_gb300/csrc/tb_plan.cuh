@@ -58,6 +58,15 @@ struct ProfRec {
     int kernels = 1;   // kernel launches between the two events
 };
 
+// Launch shape of one fused level pass picked by tb_autotune (0 = the
+// built-in rule).
+struct LevelTune {
+    int mode = 0;    // 1 = the per-mode launches won the tuning, 2 = the fused launch
+    int vc = 0;      // right-hand sides per work item
+    int cps = 0;     // resident thread blocks per SM the grid is sized for
+    int obmax = 0;   // largest register chunk of output rows (4 .. 16)
+};
+
 // Launch shape of one mode-product launch picked by tb_autotune (0 = the
 // built-in rule).
 struct ModeTune {
@@ -137,6 +146,9 @@ struct tb_plan {
 
     // launch shapes chosen by tb_autotune: [complex64 / complex128][side][pass][level][mode]
     tb::ModeTune tune[2][2][4][TB_MAX_LEVELS][TB_MAX_D];
+    tb::LevelTune ltune[2][4][TB_MAX_LEVELS];   // fused level passes: [side][pass][level]
+    int level_choice = 0;          // tb_options.level_schedule
+    int core_rows = 1;             // forward complex64 core with one RHS: 32 rows per warp (k_core_rows)
     int sep_choice = 0;            // separable apply: tb_options.sep_schedule
     int autotune = 0;              // tune at the first apply of each (nv, precision)
     std::vector<std::pair<int64_t, int>> tuned;   // (nv, precision) pairs tuned so far

@@ -4,7 +4,10 @@ scheduled, never what it computes.
 For a non-separable handle it picks, per level pass, side and mode, the
 output rows per register tile and the grid size; every output entry is still
 the same sum over the same fiber in the same order, so the tuned apply must
-equal the untuned one bit for bit (forward and adjoint).  For a separable
+equal the untuned one bit for bit (forward and adjoint) within one form of
+the level passes (per-mode launches, or fused launches).  With the built-in
+rule it also picks per pass the faster of the two forms, which round
+differently (FP32): there the bar is the complex64 rounding.  For a separable
 handle it picks between per-mode fiber passes and multi-mode tile passes,
 which sum in different orders: there the bar is the oracle's.
 """
@@ -35,7 +38,8 @@ def rel(a, b):
 @pytest.mark.parametrize("name,n,L,nv", [("helmholtz3d_n64", 16, 2, 3), ("radon2d_n256", 64, 4, 2)])
 def test_tuned_apply_is_bitwise_the_untuned_apply(name, n, L, nv):
     w = W.small(name, n, nv=nv, L=L)
-    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C128))
+    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C128),
+                          level_schedule=tb.LEVEL_PER_MODE)
     for prec in (tb.PREC_C64, tb.PREC_C128):
         f = W.rhs(w).to(tb.dtype_of(prec)).cuda()
         u0, v0 = op.apply(f, prec), op.apply_adjoint(f, prec)
@@ -69,4 +73,17 @@ def test_separable_choice_keeps_oracle_accuracy():
         y = y.to(torch.complex128).numpy().reshape(-1, 3)
         want = oracle.workload_apply_adjoint(w, f) if adjoint else ref
         assert rel(y, want) < 1e-5
+    op.close()
+
+
+@pytest.mark.parametrize("name,n,L,nv", [("helmholtz3d_n64", 32, 2, 3), ("radon2d_n256", 64, 4, 2)])
+def test_tuned_choice_of_level_pass_form_keeps_complex64_rounding(name, n, L, nv):
+    w = W.small(name, n, nv=nv, L=L)
+    op = tb.from_workload(w, precisions=1 << tb.PREC_C64)
+    f = W.rhs(w).to(torch.complex64).cuda()
+    u0, v0 = op.apply(f, tb.PREC_C64), op.apply_adjoint(f, tb.PREC_C64)
+    op.autotune(nv, tb.PREC_C64)
+    u1, v1 = op.apply(f, tb.PREC_C64), op.apply_adjoint(f, tb.PREC_C64)
+    for a, b in ((u1, u0), (v1, v0)):
+        assert (torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b)).item() < 1e-5
     op.close()
