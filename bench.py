@@ -55,6 +55,8 @@ def parse():
     p.add_argument("--n", type=int, default=None, help="points per axis of a reduced-size copy (profiling)")
     p.add_argument("--level-schedule", type=int, default=0,
                    help="non-separable handles: tb_options.level_schedule (0 rule, 1 per-mode, 2 fused)")
+    p.add_argument("--core-mode", type=int, default=0,
+                   help="tb_options.core_mode (0 rule, 1 stored cores, 2 regenerated in the one-RHS forward core)")
     p.add_argument("--sep-schedule", type=int, default=0,
                    help="separable handles: tb_options.sep_schedule (0 rule; the tuner may replace it)")
     return p.parse_args()
@@ -313,7 +315,8 @@ def main():
     prec = args.precision if args.precision is not None else w.precision
     mask = (1 << prec) | ((1 << tb.PREC_C128) if not args.no_fp64 else 0)
     op = tb.from_workload(w, precisions=mask, use_graphs=not args.profile_only, precision=prec,
-                          sep_schedule=args.sep_schedule, level_schedule=args.level_schedule)
+                          sep_schedule=args.sep_schedule, level_schedule=args.level_schedule,
+                          core_mode=args.core_mode)
     info = op.info()
     nv = w.nv
     tune_s = None

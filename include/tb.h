@@ -123,6 +123,14 @@ typedef struct {
                               2 = one fused persistent launch per pass (the mode products
                                   of a unit back to back, intermediates in a per-block
                                   scratch); complex128 always uses 1 */
+    int core_mode;         /* the forward complex64 mid-level core with one RHS (Alg. 2 step 2):
+                              0 = built-in rule (stored cores; tb_autotune may pick 2),
+                              1 = read the stored cores K(t-bar, s-bar),
+                              2 = evaluate K(t-bar, s-bar) at the skeleton points inside
+                                  the contraction (Helmholtz and Radon kernels on uniform
+                                  grids, where |x - y|^2 and x.xi are exact integers in
+                                  grid units; else 1).  The cores stay stored: the adjoint
+                                  and several-RHS contractions read them */
 } tb_options;
 
 typedef struct tb_plan *tb_handle;

@@ -25,6 +25,7 @@ KERNEL_FOURIER, KERNEL_HELMHOLTZ, KERNEL_RADON, KERNEL_RADON_ANISO = 1, 2, 3, 4
 PREC_C128, PREC_C64, PREC_C64_SPLITBF16 = 0, 1, 2
 SEP_RULE, SEP_FIBER, SEP_TILE, SEP_REGISTER, SEP_REGISTER_PAIRS, SEP_REGISTER_SCALAR, SEP_REGISTER_ONE = range(7)
 LEVEL_RULE, LEVEL_PER_MODE, LEVEL_FUSED = range(3)
+CORE_RULE, CORE_STORED, CORE_REGENERATE = range(3)
 ORDER_AUTO, ORDER_NATURAL, ORDER_BITREV = -1, 0, 1
 
 STATUS = {0: "TB_OK", 1: "TB_EINVAL", 2: "TB_ENOMEM", 3: "TB_ECUDA", 4: "TB_ERANK",
@@ -56,7 +57,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("order", ctypes.c_int), ("proxy_rows", ctypes.c_int),
                 ("rank_max", ctypes.c_int), ("precisions", ctypes.c_uint), ("separable", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("device", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("autotune", ctypes.c_int), ("sep_schedule", ctypes.c_int), ("level_schedule", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("sep_schedule", ctypes.c_int), ("level_schedule", ctypes.c_int),
+                ("core_mode", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -148,7 +150,7 @@ class TBOperator:
                  order: int = ORDER_AUTO, precisions: int = 0, separable: int = -1,
                  use_graphs: bool = False, proxy_rows: int = 1024, rank_max: int = 32,
                  seed: int = 0x5eed, precision: int = PREC_C64, autotune: bool = False,
-                 sep_schedule: int = 0, level_schedule: int = 0):
+                 sep_schedule: int = 0, level_schedule: int = 0, core_mode: int = 0):
         L_ = lib()
         n = [int(v) for v in (n if np.iterable(n) else [n] * d)]
         self.d, self.n, self.kind = d, n, kind
@@ -167,6 +169,7 @@ class TBOperator:
         opt.autotune = int(autotune)
         opt.sep_schedule = int(sep_schedule)
         opt.level_schedule = int(level_schedule)
+        opt.core_mode = int(core_mode)
         try:
             opt.device = _torch().cuda.current_device()
         except Exception:  # pragma: no cover

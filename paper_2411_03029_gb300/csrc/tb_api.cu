@@ -132,6 +132,7 @@ tb_status tb_options_default(tb_options *o) {
     o->autotune = 0;
     o->sep_schedule = 0;
     o->level_schedule = 0;
+    o->core_mode = 0;
     return TB_OK;
 }
 
@@ -780,6 +781,78 @@ static void mode_sizes(const tb_plan *h, int64_t mm[2]) {
     }
 }
 
+// Whether the cores can be regenerated inside the contraction with exact
+// integer distances / phases (tb_options.core_mode = 2, see CoreRegen), and
+// the parameters.  Grids must be uniform: coordinate i = x0 + i h up to 1e-12.
+static void detect_regen(tb_plan *h, const tb_grids *g) {
+    CoreRegen r;
+    std::memset(&r, 0, sizeof(r));
+    h->rg = r;
+    if (h->separable || h->d > TB_MAX_D) return;
+    const int d = h->d;
+    auto uniform = [](const double *v, int64_t n, double &x0, double &hh) {
+        x0 = v[0];
+        hh = n > 1 ? v[1] - v[0] : 1.0;
+        if (!(hh > 0)) return false;
+        for (int64_t i = 0; i < n; ++i)
+            if (std::fabs(v[i] - (x0 + (double)i * hh)) > 1e-12 * std::max(1.0, std::fabs(v[i]))) return false;
+        return true;
+    };
+    auto integer = [](double v, int &out) {
+        const double q = std::nearbyint(v);
+        if (std::fabs(v - q) > 1e-9 || std::fabs(q) > 1e6) return false;
+        out = (int)q;
+        return true;
+    };
+    if (h->ks.kind == TB_KERNEL_HELMHOLTZ) {
+        double hh = -1.0, dmax = 0.0;
+        for (int k = 0; k < d; ++k) {
+            double x0, hx, y0, hy;
+            if (!uniform(g->x[k], h->n[k], x0, hx) || !uniform(g->y[k], h->n[k], y0, hy)) return;
+            if (std::fabs(hx - hy) > 1e-12 * hx) return;
+            if (hh < 0) hh = hx;
+            if (std::fabs(hx - hh) > 1e-12 * hh) return;
+            if (!integer((y0 - x0) / hh, r.off[k])) return;
+            const double ext = (double)(h->n[k] - 1) + std::fabs((double)r.off[k]);
+            dmax += ext * ext;
+        }
+        int hp = 0;
+        if (!integer(std::sqrt(h->ks.p[1]) / hh, hp)) return;
+        r.hp2 = hp * hp;
+        if (dmax + r.hp2 >= 16777216.0) return;   // D must be exact in FP32
+        const double cyc = h->ks.p[2] * hh;         // cycles per unit of sqrt(D)
+        r.cyc_hi = (float)cyc;
+        r.cyc_lo = (float)(cyc - (double)r.cyc_hi);
+        r.inv_h = (float)(1.0 / hh);
+    } else if (h->ks.kind == TB_KERNEL_RADON) {
+        int nn = 0;
+        for (int k = 0; k < d; ++k) {
+            double x0, hx, y0, hy;
+            if (!uniform(g->x[k], h->n[k], x0, hx) || !uniform(g->y[k], h->n[k], y0, hy)) return;
+            int nk = 0;
+            if (x0 != 0.0 || !integer(1.0 / hx, nk) || std::fabs(hy - 1.0) > 1e-12) return;
+            if (nn == 0) nn = nk;
+            if (nk != nn || !integer(y0, r.xi0[k])) return;
+            r.xs[k] = h->xs[k];
+        }
+        r.n = nn;
+        r.ra = h->ks.p[0];
+        r.rb = h->ks.p[1];
+    } else {
+        return;
+    }
+    const int Lc = h->Lc;
+    for (int k = 0; k < d; ++k) {
+        r.tskel[k] = h->tgt[Lc].skel[k];
+        r.sskel[k] = h->src[Lc].skel[k];
+        r.tcap[k] = h->tgt[Lc].cap[k];
+        r.scap[k] = h->src[Lc].cap[k];
+    }
+    r.nF = ipow2(d * Lc);
+    r.kind = h->ks.kind;
+    h->rg = r;
+}
+
 static tb_status build_impl(tb_plan *h, const tb_grids *grids) {
     const int d = h->d;
     TB_TRY(dalloc(h, &h->d_err, 1));
@@ -806,6 +879,7 @@ static tb_status build_impl(tb_plan *h, const tb_grids *grids) {
     TB_TRY(build_side(h, 0));
     TB_TRY(build_side(h, 1));
     TB_TRY(build_cores(h));
+    detect_regen(h, grids);
     // apply precisions of the factors
     const bool want32 = h->precisions & ((1u << TB_PREC_C64) | (1u << TB_PREC_C64_SPLITBF16));
     for (int side = 0; side < 2; ++side) {
@@ -889,6 +963,7 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
         return fail(TB_EINVAL, "L must be even with n_k / 2^L >= 1");
     if (opt.sep_schedule < 0 || opt.sep_schedule > 6) return fail(TB_EINVAL, "sep_schedule must be in [0, 6]");
     if (opt.level_schedule < 0 || opt.level_schedule > 2) return fail(TB_EINVAL, "level_schedule must be in [0, 2]");
+    if (opt.core_mode < 0 || opt.core_mode > 2) return fail(TB_EINVAL, "core_mode must be in [0, 2]");
     int dev = opt.device;
     if (dev < 0) {
         if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "no CUDA device"); }
@@ -918,6 +993,7 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     h->autotune = opt.autotune;
     h->sep_choice = opt.sep_schedule;
     h->level_choice = opt.level_schedule;
+    h->core_mode = opt.core_mode;
     h->proxy_rows = opt.proxy_rows;
     h->rank_max = opt.rank_max;
     h->seed = opt.seed;
@@ -1486,6 +1562,18 @@ tb_status core_pass(const tb_plan *h, bool adjoint, const void *in, void *out, i
     a.smem = (size_t)(tmax * c * es);
     if (a.smem > g_smem_optin) return fail(TB_EUNSUPPORTED, "core block exceeds shared memory");
     if constexpr (std::is_same<R, float>::value) {
+        if (!adjoint && nv == 1 && h->rg.kind &&
+            (h->core_mode == 2 || (h->core_mode == 0 && h->core_regen_tuned))) {
+            CoreApplyArgs<float> b = a;
+            b.rg = h->rg;
+            b.offX = (int)tmax;     // table length (entries of the largest mid-level tile)
+            b.offB0 = (int)tmax;
+            b.smem = (size_t)tmax * (3 * sizeof(float2) + 2 * (size_t)d * sizeof(int));
+            if (b.smem <= g_smem_optin) {
+                TB_CK(launch_core_regen(b, st));
+                return TB_OK;
+            }
+        }
         if (!adjoint && nv == 1 && h->core_rows) {
             TB_CK(launch_core_rows<float>(a, st));
             return TB_OK;
@@ -1944,6 +2032,19 @@ tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, cons
     } else {
         void *B[2] = {h->ws.buf[0], h->ws.buf[1]};
         void *T[2] = {h->ws.mbuf[0], h->ws.mbuf[1]};
+        // the one-RHS forward core: stored cores against cores regenerated at the
+        // skeleton points (tb_options.core_mode = 0 only)
+        h->core_regen_tuned = 0;
+        if (std::is_same<R, float>::value && nv == 1 && h->rg.kind && h->core_mode == 0 &&
+            precision == TB_PREC_C64) {
+            float t_st = 0.f, t_rg = 0.f;
+            status = time_it([&] { return core_pass<R>(h, false, B[0], B[1], nv, st, precision); }, t_st);
+            if (status == TB_OK) {
+                h->core_regen_tuned = 1;
+                status = time_it([&] { return core_pass<R>(h, false, B[0], B[1], nv, st, precision); }, t_rg);
+                h->core_regen_tuned = (status == TB_OK && t_rg < t_st) ? 1 : 0;
+            }
+        }
         // fused level passes (complex64): RHS per work item, blocks per SM and
         // output rows per register chunk; every candidate accumulates each
         // output in the same order, so the choice does not change results

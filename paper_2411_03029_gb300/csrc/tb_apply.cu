@@ -299,15 +299,17 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core_dense(const CoreApplyArgs
 }
 
 // Forward core for one right-hand side, complex64: G_{t,s}[a] = sum_b C[a][b] F_{t,s}[b].
-// A warp takes 32 core rows at a time; lane l takes columns l, l + 32, .. and
-// accumulates all 32 rows, reading each row
-// coalesced (32 consecutive entries per load, 32 independent loads in flight
-// per lane); a transposed butterfly reduction (31 exchanges per component for
-// the 32 rows) then leaves row r0 + l's sum in lane l.  Columns of a row are
-// summed in the same order for every row (lane-strided partial sums, then the
-// butterfly): deterministic.
+// A warp takes CR_ROWS core rows at a time; lane l takes columns l, l + 32, ..
+// and accumulates all CR_ROWS rows, reading each row coalesced (32 consecutive
+// entries per load, CR_ROWS independent loads in flight per lane).  A
+// transposed butterfly reduction (CR_ROWS - 1 exchanges per component within
+// each half-warp, then one across the halves) leaves row r0 + l's sum in lanes
+// l and l + 16.  Columns of a row are summed in the same order for every row:
+// deterministic.
+constexpr int CR_ROWS = 16;
+
 template <class R>
-__global__ void __launch_bounds__(CORE_THREADS) k_core_rows(const CoreApplyArgs<R> a) {
+__global__ void __launch_bounds__(CORE_THREADS, 3) k_core_rows(const CoreApplyArgs<R> a) {
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<R> *Xc = reinterpret_cast<cx<R> *>(smraw);
     const int d = a.d;
@@ -336,27 +338,31 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core_rows(const CoreApplyArgs<
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nk = (Ms + 31) >> 5;
-    for (int r0 = warp * 32; r0 < Mt; r0 += nw * 32) {
-        cx<R> acc[32];
+    for (int r0 = warp * CR_ROWS; r0 < Mt; r0 += nw * CR_ROWS) {
+        cx<R> acc[CR_ROWS];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) acc[j] = {R(0), R(0)};
-        const int nr = Mt - r0 < 32 ? Mt - r0 : 32;
-#pragma unroll 1
+        for (int j = 0; j < CR_ROWS; ++j) acc[j] = {R(0), R(0)};
+        const int nr = Mt - r0 < CR_ROWS ? Mt - r0 : CR_ROWS;
         for (int k = 0; k < nk; ++k) {
             const int b = lane + 32 * k;
             const bool live = b < Ms;
             const cx<R> *col = C + (int64_t)r0 * Ms + b;
             const cx<R> xk = live ? Xc[b] : cx<R>{R(0), R(0)};
+            cx<R> c[CR_ROWS];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const cx<R> c = (live && j < nr) ? col[(int64_t)j * Ms] : cx<R>{R(0), R(0)};
-                cmac(acc[j], c, xk);
+            for (int j = 0; j < CR_ROWS; ++j) {
+                // the core is read once per apply: streaming loads (evict first)
+                float2 v = make_float2(0.f, 0.f);
+                if (live && j < nr) v = __ldcs(reinterpret_cast<const float2 *>(col + (int64_t)j * Ms));
+                c[j] = cx<R>{v.x, v.y};
             }
-        }
-        // transposed reduction: after the step with offset o, lane l keeps the
-        // partial sums of the rows whose bit o equals lane bit o
 #pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
+            for (int j = 0; j < CR_ROWS; ++j) cmac(acc[j], c[j], xk);
+        }
+        // transposed reduction within each half-warp: after the step with offset
+        // o, lane l keeps the partial sums of the rows whose bit o equals lane bit o
+#pragma unroll
+        for (int o = CR_ROWS / 2; o >= 1; o >>= 1) {
             const bool up = (lane & o) != 0;
 #pragma unroll
             for (int j = 0; j < o; ++j) {
@@ -368,6 +374,8 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core_rows(const CoreApplyArgs<
                 acc[j] = {keep.x + got.x, keep.y + got.y};
             }
         }
+        acc[0].x += __shfl_xor_sync(0xffffffffu, acc[0].x, 16);
+        acc[0].y += __shfl_xor_sync(0xffffffffu, acc[0].y, 16);
         if (lane < nr) {
             int q = r0 + lane, pos = 0, stride = 1;
             for (int k = d - 1; k >= 0; --k) {
@@ -378,6 +386,168 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core_rows(const CoreApplyArgs<
             dst[(int64_t)pos * a.nv] = acc[0];
         }
     }
+}
+
+// Forward core for one RHS with the entries of K(t-bar, s-bar) evaluated on
+// the fly (no core bytes read), same row batches and reduction as k_core_rows.
+// The block builds per-row and per-column tables of the pair's skeleton points
+// (integer grid coordinates, and for the Radon kernel c(x) and |xi| as FP32
+// double-floats from FP64), then each entry costs integer arithmetic, one
+// residual-corrected sqrt and one sincospif:
+//   sqrt(D) = s + (D - s^2) / (2 s)  (D an exact integer in FP32, the residual by FMA),
+//   phase = cyc (s + s_lo) as a double-float product (Dekker: p = c s and its
+//   exact error fma(c, s, -p)), reduced to (-1/2, 1/2] cycles before sincospif.
+template <int KIND>
+__global__ void __launch_bounds__(CORE_THREADS, 3) k_core_regen(const CoreApplyArgs<float> a) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int d = a.d;
+    const int64_t p = blockIdx.x;
+    int rt[MAXD], rs[MAXD];
+    int Mt = 1, Ms = 1;
+    for (int k = 0; k < d; ++k) {
+        rt[k] = a.dims[p * 2 * d + k];
+        rs[k] = a.dims[p * 2 * d + d + k];
+        Mt *= rt[k];
+        Ms *= rs[k];
+    }
+    // shared tables: X (Ms), column ints (Ms x d), column float pair (Ms), row ints (Mt x d), row float pair (Mt)
+    cx<float> *Xc = reinterpret_cast<cx<float> *>(smraw);
+    float2 *colf = reinterpret_cast<float2 *>(Xc + a.offX);
+    float2 *rowf = colf + a.offX;
+    int *coli = reinterpret_cast<int *>(rowf + a.offB0);
+    int *rowi = coli + (int64_t)a.offX * d;
+    const CoreRegen &g = a.rg;
+    const int64_t t = p / g.nF, s = p - t * g.nF;
+    const int64_t jt = t * g.nF + s, js = s * g.nF + t;
+    const cx<float> *src = a.in.p + p * a.in.tsize * a.nv;
+    cx<float> *dst = a.out.p + p * a.out.tsize * a.nv;
+    for (int b = threadIdx.x; b < Ms; b += blockDim.x) {
+        int q = b, pos = 0, stride = 1;
+        double xx = 0.0;
+        for (int k = d - 1; k >= 0; --k) {
+            const int bk = q % rs[k];
+            q /= rs[k];
+            pos += bk * stride;
+            stride *= a.in.R[k];
+            const int j = g.sskel[k][js * g.scap[k] + bk];
+            const int v = KIND == TB_KERNEL_HELMHOLTZ ? j + g.off[k] : j + g.xi0[k];
+            coli[(int64_t)b * d + k] = v;
+            xx += (double)v * v;
+        }
+        Xc[b] = src[(int64_t)pos * a.nv];
+        if (KIND == TB_KERNEL_RADON) {
+            const double nr = sqrt(xx);
+            const float hi = (float)nr;
+            colf[b] = make_float2(hi, (float)(nr - hi));
+        }
+    }
+    for (int r = threadIdx.x; r < Mt; r += blockDim.x) {
+        int q = r;
+        double sp = 1.0;
+        for (int k = d - 1; k >= 0; --k) {
+            const int ak = q % rt[k];
+            q /= rt[k];
+            const int i = g.tskel[k][jt * g.tcap[k] + ak];
+            rowi[(int64_t)r * d + k] = i;
+            if (KIND == TB_KERNEL_RADON) sp *= sinpi(2.0 * g.xs[k][i]);
+        }
+        if (KIND == TB_KERNEL_RADON) {
+            const double c = g.ra + g.rb * sp;
+            const float hi = (float)c;
+            rowf[r] = make_float2(hi, (float)(c - hi));
+        }
+    }
+    for (int e = threadIdx.x; e < a.out.tsize; e += blockDim.x) dst[(int64_t)e * a.nv] = {0.f, 0.f};
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nk = (Ms + 31) >> 5;
+    for (int r0 = warp * CR_ROWS; r0 < Mt; r0 += nw * CR_ROWS) {
+        cx<float> acc[CR_ROWS];
+#pragma unroll
+        for (int j = 0; j < CR_ROWS; ++j) acc[j] = {0.f, 0.f};
+        const int nr = Mt - r0 < CR_ROWS ? Mt - r0 : CR_ROWS;
+        for (int k = 0; k < nk; ++k) {
+            const int b = lane + 32 * k;
+            const bool live = b < Ms;
+            const int bb = live ? b : 0;
+            const cx<float> xk = live ? Xc[b] : cx<float>{0.f, 0.f};
+            int cj[MAXD];
+            for (int m = 0; m < d; ++m) cj[m] = coli[(int64_t)bb * d + m];
+            const float2 cf = KIND == TB_KERNEL_RADON ? colf[bb] : make_float2(0.f, 0.f);
+#pragma unroll 4
+            for (int j = 0; j < CR_ROWS; ++j) {
+                if (j >= nr) break;
+                const int r = r0 + j;
+                float sn, cs, amp = 1.f;
+                if (KIND == TB_KERNEL_HELMHOLTZ) {
+                    int D = g.hp2;
+                    for (int m = 0; m < d; ++m) {
+                        const int dd = rowi[(int64_t)r * d + m] - cj[m];
+                        D += dd * dd;
+                    }
+                    const float Df = (float)D;
+                    const float sq = sqrtf(Df);
+                    const float slo = fmaf(-sq, sq, Df) / (2.f * sq);
+                    const float ph = g.cyc_hi * sq;
+                    const float er = fmaf(g.cyc_hi, sq, -ph);
+                    const float lo = fmaf(g.cyc_hi, slo, fmaf(g.cyc_lo, sq, er));
+                    const float f = (ph - rintf(ph)) + lo;
+                    sincospif(2.f * f, &sn, &cs);
+                    amp = g.inv_h / sq;
+                } else {
+                    int num = 0;
+                    for (int m = 0; m < d; ++m) num += rowi[(int64_t)r * d + m] * cj[m];
+                    int md = num % g.n;
+                    if (md < 0) md += g.n;
+                    const float f1 = (float)md / (float)g.n;
+                    const float2 rc = rowf[r];
+                    const float ph = rc.x * cf.x;
+                    const float er = fmaf(rc.x, cf.x, -ph);
+                    const float lo = fmaf(rc.x, cf.y, fmaf(rc.y, cf.x, er));
+                    float f = f1 + ((ph - rintf(ph)) + lo);
+                    f -= rintf(f);
+                    sincospif(2.f * f, &sn, &cs);
+                }
+                const cx<float> kv = {live ? cs * amp : 0.f, live ? sn * amp : 0.f};
+                cmac(acc[j], kv, xk);
+            }
+        }
+#pragma unroll
+        for (int o = CR_ROWS / 2; o >= 1; o >>= 1) {
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int j = 0; j < o; ++j) {
+                const cx<float> send = up ? acc[j] : acc[j + o];
+                const cx<float> keep = up ? acc[j + o] : acc[j];
+                cx<float> got;
+                got.x = __shfl_xor_sync(0xffffffffu, send.x, o);
+                got.y = __shfl_xor_sync(0xffffffffu, send.y, o);
+                acc[j] = {keep.x + got.x, keep.y + got.y};
+            }
+        }
+        acc[0].x += __shfl_xor_sync(0xffffffffu, acc[0].x, 16);
+        acc[0].y += __shfl_xor_sync(0xffffffffu, acc[0].y, 16);
+        if (lane < nr) {
+            int q = r0 + lane, pos = 0, stride = 1;
+            for (int k = d - 1; k >= 0; --k) {
+                pos += (q % rt[k]) * stride;
+                q /= rt[k];
+                stride *= a.out.R[k];
+            }
+            dst[(int64_t)pos * a.nv] = acc[0];
+        }
+    }
+}
+
+cudaError_t launch_core_regen(const CoreApplyArgs<float> &a, cudaStream_t st) {
+    void (*fn)(const CoreApplyArgs<float>) = nullptr;
+    if (a.rg.kind == TB_KERNEL_HELMHOLTZ) fn = k_core_regen<TB_KERNEL_HELMHOLTZ>;
+    else if (a.rg.kind == TB_KERNEL_RADON) fn = k_core_regen<TB_KERNEL_RADON>;
+    else return cudaErrorInvalidValue;
+    cudaError_t e = set_smem_once((const void *)fn, a.smem);
+    if (e != cudaSuccess) return e;
+    fn<<<(unsigned)a.P, CORE_THREADS, a.smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 template <class R>

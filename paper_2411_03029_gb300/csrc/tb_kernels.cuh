@@ -183,6 +183,28 @@ bool level_ob_valid(int ob);
 int level_threads();
 int level_max_children();
 
+// Regeneration of the mid-level cores K(t-bar, s-bar) from the skeleton points
+// inside the one-RHS forward core (k_core_regen), for the kernels whose
+// distances or phases are exact integers on uniform grids:
+//   HELMHOLTZ on x_k = x0_k + i h, y_k = x0_k + (j + off_k) h (one spacing h and
+//     integer offsets): |x - y|^2 + hperp^2 = h^2 D with the integer
+//     D = sum_k (i_k - j_k - off_k)^2 + hp2 < 2^24, phase (cycles) = cyc sqrt(D);
+//   RADON on x_k = i / n, xi_k = j + xi0_k (integers): x.xi = (sum i_k xi_k) / n,
+//     phase = x.xi + c(x) |xi|, c(x) = a + b prod_k sin(2 pi x_k) per target row.
+struct CoreRegen {
+    int kind;                       // 0: cores are read; TB_KERNEL_HELMHOLTZ or TB_KERNEL_RADON
+    int off[MAXD], hp2;             // Helmholtz integer offsets and perpendicular offset^2 (grid units)
+    float cyc_hi, cyc_lo;           // kappa h / (2 pi) as a double-float
+    float inv_h;
+    int n;                          // Radon: target grid denominator
+    int xi0[MAXD];                  // Radon: integer source offsets
+    double ra, rb;                  // Radon: c(x) = ra + rb prod sin(2 pi x_k)
+    const double *xs[MAXD];         // target coordinates (Radon c(x) in FP64)
+    const int *tskel[MAXD], *sskel[MAXD];   // level-Lc skeleton grid indices
+    int tcap[MAXD], scap[MAXD];
+    int64_t nF;
+};
+
 template <class R>
 struct CoreApplyArgs {
     int d;
@@ -196,6 +218,7 @@ struct CoreApplyArgs {
     int Lc;
     int offX, offB0, offB1, offY, offA;
     size_t smem;
+    CoreRegen rg;
 };
 
 // Split-BF16 tensor-core core contraction (tb_core_tc.cu).  A work item is one
@@ -424,9 +447,11 @@ template <class R>
 cudaError_t launch_core_dense(bool adjoint, const CoreApplyArgs<R> &a, cudaStream_t st);
 template <class R>
 cudaError_t launch_core_kron(bool adjoint, const CoreApplyArgs<R> &a, cudaStream_t st);
-// Forward core for one RHS, complex64, 32 rows per warp (k_core_rows).
+// Forward core for one RHS, complex64, 16 rows per warp (k_core_rows); the
+// same with the core entries regenerated from the skeleton points (k_core_regen).
 template <class R>
 cudaError_t launch_core_rows(const CoreApplyArgs<R> &a, cudaStream_t st);
+cudaError_t launch_core_regen(const CoreApplyArgs<float> &a, cudaStream_t st);
 
 // Shared-memory plan of a mode-product chain: input dims m, output dims o.
 struct ChainSmem {

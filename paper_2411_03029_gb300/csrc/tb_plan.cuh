@@ -148,7 +148,10 @@ struct tb_plan {
     tb::ModeTune tune[2][2][4][TB_MAX_LEVELS][TB_MAX_D];
     tb::LevelTune ltune[2][4][TB_MAX_LEVELS];   // fused level passes: [side][pass][level]
     int level_choice = 0;          // tb_options.level_schedule
-    int core_rows = 1;             // forward complex64 core with one RHS: 32 rows per warp (k_core_rows)
+    int core_rows = 1;             // forward complex64 core with one RHS: row batches per warp (k_core_rows)
+    int core_mode = 0;             // tb_options.core_mode
+    int core_regen_tuned = 0;      // tb_autotune found the regenerated core faster
+    tb::CoreRegen rg{};            // regeneration parameters (rg.kind = 0: not possible)
     int sep_choice = 0;            // separable apply: tb_options.sep_schedule
     int autotune = 0;              // tune at the first apply of each (nv, precision)
     std::vector<std::pair<int64_t, int>> tuned;   // (nv, precision) pairs tuned so far
