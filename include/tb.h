@@ -291,6 +291,42 @@ tb_status tb_cgls(tb_handle h, const void *b, void *x, int64_t nv, int iters, in
                   double *resid, void *cuda_stream);
 
 /*
+ * Partitioned apply, for running one operator over several devices (one
+ * handle per device, each built with the same arguments).  Steps 1 and 3 of
+ * Alg. 2 are independent per mid-level source multi-set s and per mid-level
+ * target multi-set t (Sec. 3.2); the only coupling is the mid-level tensor of
+ * the (t, s) pairs, so rank g takes a range S_g of the s and a range T_g of the
+ * t, and one exchange of mid-level tiles connects the halves:
+ *   tb_apply_src_part  steps 1 and 2 for s in [s_begin, s_end): reads the source
+ *                      points of those s from f (the tb_apply layout), writes the
+ *                      tiles G_{t,s} of every t and those s into g_mid;
+ *   exchange           tile (t, s) goes from the owner of s to the owner of t;
+ *   tb_apply_tgt_part  step 3 for t in [t_begin, t_end): reads the tiles (t, s)
+ *                      of those t and every s from g_mid, writes the target points
+ *                      of those t into u (other entries of u are left as they are).
+ * g_mid is a device array of nF x nF tiles (nF = 2^(d Lc), tb_info.Lc) of
+ * prod_k tb_info.rank_tgt[Lc][k] entries x nv each (element type of the
+ * precision), tile (t, s) at position t nF + s, t and s the flat mid-level
+ * multi-set indices (mode 0 most significant), entries in C order over the
+ * padded ranks with the RHS innermost: for fixed t, the tiles of a range of s
+ * are contiguous.  Complex128 and complex64 (TB_PREC_C64) only; the handle's
+ * workspaces are used as in tb_apply (calls on one handle are stream-ordered).
+ * Errors: TB_EINVAL (bad handle, range, pointers), TB_EUNSUPPORTED (separable
+ * handle, split-BF16 or a precision not built), TB_ECUDA.
+ */
+tb_status tb_apply_src_part(tb_handle h, const void *f, void *g_mid, int64_t nv, int64_t s_begin, int64_t s_end,
+                            int precision, void *cuda_stream);
+tb_status tb_apply_tgt_part(tb_handle h, const void *g_mid, void *u, int64_t nv, int64_t t_begin, int64_t t_end,
+                            int precision, void *cuda_stream);
+
+/*
+ * The partition of the nmid mid-level multi-sets over nranks ranks: contiguous
+ * ranges [begin[g], end[g]) of near-equal size (the same plan serves the s and
+ * the t ranges).  Host only.  TB_EINVAL for nmid < 1, nranks < 1 or NULL arrays.
+ */
+tb_status tb_shard_plan(int64_t nmid, int nranks, int64_t *begin, int64_t *end);
+
+/*
  * Empirical tuning of the apply's launch shapes for nv right-hand sides at
  * `precision`, on the handle's own factors and workspaces (the paper fixes no
  * launch layout; this is the library's own schedule search):

@@ -7,7 +7,9 @@ documented with tb_export_factors / tb_export_cores in include/tb.h) and
 applies them exactly as the paper writes the method, so the GPU apply can be
 compared with it to rounding, independently of the ID's approximation error.
 
-  apply(bf, f)          Alg. 2 (contraction), steps (1) - (3) in the paper's order:
+  apply(bf, f)          Alg. 2 (contraction), steps (1) - (3) in the paper's order
+                        (source_part: steps (1)-(2) for a range of mid-level source
+                        multi-sets; target_part: step (3) for a range of target ones):
                         (1) F_{tau,s} for l = 0..Lc: F(s) x_k V-bar^{s,k} at l = 0,
                             F_{p_tau,s} x_k diag_nu(W^{s,k}_{tau,nu}) at l > 0;
                         (2) G_{t,s} = K(t-bar, s-bar) x_{d+1..2d} F_{t,s};
@@ -128,26 +130,26 @@ def _ix(B, node_idx):
 
 
 # -------------------------------------------------------------------- apply
-def apply(bf, f) -> np.ndarray:
-    """u = K_BF f, Alg. 2.  f: (n_1..n_d, nv) (or without the RHS axis)."""
+def source_part(bf, f, s_range=None) -> dict:
+    """Steps (1) and (2) of Alg. 2 for the mid-level source multi-sets s in
+    s_range = (begin, end) (all if None): {(t, s): G_{t,s}} for every t and those s."""
     B = _Bf(bf)
     d, Lc = B.d, B.Lc
     f = np.asarray(f, dtype=np.complex128)
-    squeeze = f.ndim == d
-    if squeeze:
+    if f.ndim == d:
         f = f[..., None]
     nv = f.shape[-1]
-    nb = 1 << Lc
+    srange = range(B.nF) if s_range is None else range(int(s_range[0]), int(s_range[1]))
     # (1) source side, l = 0 .. Lc: F[(tau, s)]
     F = {}
-    for s in range(B.nF):
+    for s in srange:
         X = f[_ix(B, _unflat(s, Lc, d))]
         for k in range(d):
             X = _mode(X, B.diag(0, 0, k, s, 0), k)
         F[(0, s)] = X
     for l in range(1, Lc + 1):
         Fn = {}
-        for s in range(B.nF):
+        for s in srange:
             for tau in range(1 << (d * l)):
                 X = F[(_parent(tau, l, d), s)]
                 for k in range(d):
@@ -157,15 +159,26 @@ def apply(bf, f) -> np.ndarray:
     # (2) mid-level cores: G_{t,s} = K(t-bar, s-bar) x F_{t,s}
     G = {}
     for t in range(B.nF):
-        for s in range(B.nF):
+        for s in srange:
             C, rt, rs = B.core_block(t, s)
             X = F[(t, s)]
             assert list(X.shape[:d]) == rs, "core source dims differ from F_{t,s}"
             G[(t, s)] = (C @ X.reshape(-1, nv)).reshape(*rt, nv)
-    # (3) target side, l = Lc .. 1: G_{t,p_nu} += G_{t,nu} x_k diag_tau(P)^T; l = 0: U-bar^T
+    return G
+
+
+def target_part(bf, G, t_range=None, out=None) -> np.ndarray:
+    """Step (3) of Alg. 2 for the mid-level target multi-sets t in t_range (all if
+    None) from the tiles G[(t, s)] of those t and every s: writes their target
+    points into `out` (a zero tensor of the target grid's shape + nv if None)."""
+    B = _Bf(bf)
+    d, Lc = B.d, B.Lc
+    nv = next(iter(G.values())).shape[-1]
+    trange = range(B.nF) if t_range is None else range(int(t_range[0]), int(t_range[1]))
+    G = {key: val for key, val in G.items() if key[0] in trange}
     for l in range(Lc, 0, -1):
         Gn = {}
-        for t in range(B.nF):
+        for t in trange:
             for nu in range(1 << (d * l)):
                 X = G[(t, nu)]
                 for k in range(d):
@@ -173,13 +186,20 @@ def apply(bf, f) -> np.ndarray:
                 key = (t, _parent(nu, l, d))
                 Gn[key] = Gn[key] + X if key in Gn else X
         G = Gn
-    u = np.zeros(tuple(B.n) + (nv,), dtype=np.complex128)
-    for t in range(B.nF):
+    u = np.zeros(tuple(B.n) + (nv,), dtype=np.complex128) if out is None else out
+    for t in trange:
         X = G[(t, 0)]
         for k in range(d):
             X = _mode(X, B.diag(1, 0, k, t, 0).T, k)
         u[_ix(B, _unflat(t, Lc, d))] = X
-    assert nb == 1 << Lc
+    return u
+
+
+def apply(bf, f) -> np.ndarray:
+    """u = K_BF f, Alg. 2: steps (1) - (2) for every source multi-set, then step (3)."""
+    d = int(bf["d"])
+    squeeze = np.asarray(f).ndim == d
+    u = target_part(bf, source_part(bf, f))
     return u[..., 0] if squeeze else u
 
 

@@ -36,7 +36,8 @@ EXPORTS = ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_appl
            "tb_apply_host", "tb_query", "tb_free", "tb_last_error", "tb_version",
            "tb_profile_enable", "tb_profile_stats", "tb_apply_noalloc", "tb_autotune", "tb_apply_host_batch",
            "tb_alu_peak", "tb_cgls",
-           "tb_export_factors", "tb_export_cores", "tb_export_order")
+           "tb_export_factors", "tb_export_cores", "tb_export_order",
+           "tb_apply_src_part", "tb_apply_tgt_part", "tb_shard_plan")
 
 
 class TBError(RuntimeError):
@@ -119,10 +120,14 @@ def lib():
         L.tb_export_factors.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]
         L.tb_export_cores.argtypes = [P, P, P, P, P, P]
         L.tb_export_order.argtypes = [P, ctypes.c_int, P]
+        L.tb_apply_src_part.argtypes = [P, P, P, I64, I64, I64, ctypes.c_int, P]
+        L.tb_apply_tgt_part.argtypes = [P, P, P, I64, I64, I64, ctypes.c_int, P]
+        L.tb_shard_plan.argtypes = [I64, ctypes.c_int, P, P]
         for name in ("tb_options_default", "tb_build", "tb_build_ex", "tb_apply", "tb_apply_adjoint",
                      "tb_apply_host", "tb_query", "tb_free", "tb_profile_enable", "tb_profile_stats",
                      "tb_apply_noalloc", "tb_apply_host_batch", "tb_alu_peak", "tb_cgls",
-                     "tb_export_factors", "tb_export_cores", "tb_export_order"):
+                     "tb_export_factors", "tb_export_cores", "tb_export_order",
+                     "tb_apply_src_part", "tb_apply_tgt_part", "tb_shard_plan"):
             getattr(L, name).restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -322,6 +327,38 @@ class TBOperator:
         out.update(core_offsets=offs, core_dims=dims, core=core)
         return out
 
+    # ------------------------------------------------------ partitioned apply
+    def mid_shape(self, nv: int) -> tuple:
+        """Shape (nF, nF, tile entries, nv) of the mid-level tensor exchanged by a
+        partitioned apply (tb_apply_src_part / tb_apply_tgt_part)."""
+        inf = self.info()
+        nF = 2 ** (inf["d"] * inf["Lc"])
+        return (nF, nF, int(np.prod(inf["rank_tgt"][inf["Lc"]])), int(nv))
+
+    def apply_src_part(self, f, g_mid, s_range, precision: int | None = None):
+        """Steps 1 and 2 of Alg. 2 for the mid-level source multi-sets in s_range = (begin, end):
+        writes the mid-level tiles (t, s) of those s into g_mid (tb_apply_src_part)."""
+        torch = _torch()
+        f, precision, _ = self._prep(f, precision)
+        stream = torch.cuda.current_stream(f.device).cuda_stream
+        _check(lib().tb_apply_src_part(self._h, ctypes.c_void_p(f.data_ptr()), ctypes.c_void_p(g_mid.data_ptr()),
+                                       f.shape[-1], int(s_range[0]), int(s_range[1]), precision,
+                                       ctypes.c_void_p(stream)))
+        return g_mid
+
+    def apply_tgt_part(self, g_mid, u, t_range, precision: int | None = None):
+        """Step 3 of Alg. 2 for the mid-level target multi-sets in t_range: writes the target
+        points of those t into u (tb_apply_tgt_part)."""
+        torch = _torch()
+        u_, precision, _ = self._prep(u, precision)
+        if u_.data_ptr() != u.data_ptr():
+            raise ValueError("u must be a contiguous tensor of the apply layout")
+        stream = torch.cuda.current_stream(u.device).cuda_stream
+        _check(lib().tb_apply_tgt_part(self._h, ctypes.c_void_p(g_mid.data_ptr()), ctypes.c_void_p(u.data_ptr()),
+                                       u_.shape[-1], int(t_range[0]), int(t_range[1]), precision,
+                                       ctypes.c_void_p(stream)))
+        return u
+
     def apply_host_batch(self, fs, us, precision: int | None = None):
         """u_i = K f_i for lists of host arrays (numpy, pinned for overlap), with the
         copies of neighbouring inputs and results overlapping the applies
@@ -349,6 +386,67 @@ class TBOperator:
         _check(lib().tb_apply_host(self._h, ctypes.c_void_p(f.ctypes.data), ctypes.c_void_p(u.ctypes.data),
                                    nv, precision))
         return u
+
+
+def shard_plan(nmid: int, nranks: int):
+    """Contiguous near-equal ranges [(begin, end)] of nmid mid-level multi-sets over nranks
+    ranks (tb_shard_plan; host only)."""
+    b = (ctypes.c_int64 * nranks)()
+    e = (ctypes.c_int64 * nranks)()
+    _check(lib().tb_shard_plan(int(nmid), int(nranks), b, e))
+    return [(b[g], e[g]) for g in range(nranks)]
+
+
+def sharded_apply(op, f, precision: int | None = None, group=None):
+    """u = K f with the work partitioned over the ranks of a torch.distributed group,
+    one operator (device) per rank (Sec. 3.2: steps 1 and 3 of Alg. 2 are independent per
+    mid-level multi-set; the mid-level tiles are the one exchange):
+
+      1. rank g runs steps 1-2 for its source range S_g (op.apply_src_part);
+      2. the tiles (t, s), t in T_h, s in S_g, go to rank h: point-to-point
+         sends and receives of contiguous blocks (all ranks at once);
+      3. rank g runs step 3 for its target range T_g (op.apply_tgt_part).
+
+    f must hold at least the source points of S_g.  Returns this rank's u: the
+    target points of T_g are set, the others are zero (sum over the ranks for
+    the whole result).  `op` needs apply_src_part, apply_tgt_part and
+    mid_shape; tensors live on the device of f."""
+    torch = _torch()
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    nv = f.shape[-1] if f.dim() == len(op.n) + 1 else 1
+    shape = op.mid_shape(nv)
+    nF = shape[0]
+    plan = shard_plan(nF, world)
+    dt = f.dtype
+    g_mid = torch.zeros(shape, dtype=dt, device=f.device)
+    s0, s1 = plan[rank]
+    op.apply_src_part(f, g_mid, (s0, s1), precision)
+    t0, t1 = plan[rank]
+    reqs, recv = [], []
+    for h in range(world):
+        th0, th1 = plan[h]
+        sh0, sh1 = plan[h]
+        if h == rank:
+            continue
+        # complex tiles travel as their real views (re, im pairs)
+        send = torch.view_as_real(g_mid[th0:th1, s0:s1].contiguous())
+        buf = torch.empty((t1 - t0, sh1 - sh0) + tuple(shape[2:]), dtype=dt, device=f.device)
+        peer = dist.get_global_rank(group, h) if group is not None else h
+        if send.numel():
+            reqs.append(dist.isend(send, dst=peer, group=group))
+        if buf.numel():
+            reqs.append(dist.irecv(torch.view_as_real(buf), src=peer, group=group))
+        recv.append((sh0, sh1, buf, send))
+    for r in reqs:
+        r.wait()
+    for sh0, sh1, buf, _ in recv:
+        if buf.numel():
+            g_mid[t0:t1, sh0:sh1] = buf
+    u = torch.zeros_like(f)
+    op.apply_tgt_part(g_mid, u, (t0, t1), precision)
+    return u
 
 
 def alu_peak(precision: int = PREC_C64) -> float:

@@ -1157,11 +1157,14 @@ int mode_ob_rule(int o) {
 // ping-pong buffers of the mode intermediates.
 template <class R>
 tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out, int64_t nv,
-                     cudaStream_t st, void *const *T, int only_k = -1, int ob_set = 0, int waves_set = 0) {
+                     cudaStream_t st, void *const *T, int only_k = -1, int ob_set = 0, int waves_set = 0,
+                     int64_t f0 = 0, int64_t f1 = -1) {
     const int d = h->d, Lc = h->Lc;
     const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
     ModeArgs<R> a;
     std::memset(&a, 0, sizeof(a));
+    a.f0 = f0;
+    a.f1 = f1 < 0 ? ipow2(d * Lc) : f1;
     a.d = d;
     a.Lc = Lc;
     a.pass = (int)pass;
@@ -1527,11 +1530,13 @@ tb_status core_pass_tc(const tb_plan *h, bool adjoint, const void *in, void *out
 
 template <class R>
 tb_status core_pass(const tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st,
-                    int precision) {
+                    int precision, int64_t pf0 = 0, int64_t pf1 = -1) {
     const int d = h->d, Lc = h->Lc;
     if (precision == TB_PREC_C64_SPLITBF16 && !h->separable) return core_pass_tc(h, adjoint, in, out, nv, st);
     CoreApplyArgs<R> a;
     std::memset(&a, 0, sizeof(a));
+    a.pf0 = pf0;
+    a.pf1 = pf1 < 0 ? ipow2(d * Lc) : pf1;
     a.d = d;
     a.P = h->P;
     a.nv = nv;
@@ -2269,6 +2274,85 @@ extern "C" tb_status tb_autotune(tb_handle h, int64_t nv, int precision, void *s
     cudaFree(uin);
     cudaFree(uout);
     return s;
+}
+
+// ---------------------------------------------- partitioned (sharded) apply
+namespace {
+
+// One half of Alg. 2 restricted to a range of mid-level multisets:
+// half 0 = steps 1 and 2 for the source multisets s in [f0, f1) (user tensor
+// -> target-side mid-level tensor, tiles (t, s) for every t); half 1 = step 3
+// for the target multisets t in [f0, f1) (mid-level tensor -> user tensor).
+// Per-mode level launches (each unit outside the range returns at once).
+template <class R>
+tb_status run_half(tb_plan *h, int half, const void *in, void *out, int64_t nv, cudaStream_t st, int precision,
+                   int64_t f0, int64_t f1) {
+    void *B[2] = {h->ws.buf[0], h->ws.buf[1]};
+    void *T[2] = {h->ws.mbuf[0], h->ws.mbuf[1]};
+    const int Lc = h->Lc;
+    if (half == 0) {
+        int cur = 0;
+        TB_TRY(level_pass<R>(h, Pass::LeafIn, false, 0, 0, in, B[cur], nv, st, T, -1, 0, 0, f0, f1));
+        for (int l = 1; l <= Lc; ++l) {
+            TB_TRY(level_pass<R>(h, Pass::Split, false, 0, l, B[cur], B[cur ^ 1], nv, st, T, -1, 0, 0, f0, f1));
+            cur ^= 1;
+        }
+        return core_pass<R>(h, false, B[cur], out, nv, st, precision, f0, f1);
+    }
+    int cur = 0;
+    const void *src = in;
+    for (int l = Lc; l >= 1; --l) {
+        TB_TRY(level_pass<R>(h, Pass::Gather, false, 1, l, src, B[cur], nv, st, T, -1, 0, 0, f0, f1));
+        src = B[cur];
+        cur ^= 1;
+    }
+    return level_pass<R>(h, Pass::LeafOut, false, 1, 0, src, out, nv, st, T, -1, 0, 0, f0, f1);
+}
+
+tb_status part_common(tb_handle h, int half, const void *in, void *out, int64_t nv, int64_t f0, int64_t f1,
+                      int precision, void *stream) {
+    if (!h) return fail(TB_EINVAL, "handle is NULL");
+    if (nv <= 0) return fail(TB_EINVAL, "nv must be positive");
+    if (h->separable) return fail(TB_EUNSUPPORTED, "partitioned applies are built for non-separable handles");
+    if (precision != TB_PREC_C128 && precision != TB_PREC_C64)
+        return fail(TB_EUNSUPPORTED, "partitioned applies support TB_PREC_C128 and TB_PREC_C64");
+    if (!(h->precisions & (1u << precision)))
+        return fail(TB_EUNSUPPORTED, "handle was built without precision " + std::to_string(precision));
+    const int64_t nF = ipow2(h->d * h->Lc);
+    if (f0 < 0 || f1 > nF || f0 > f1) return fail(TB_EINVAL, "multiset range outside [0, 2^(d Lc)]");
+    TB_TRY(check_device_ptr(in, "input"));
+    TB_TRY(check_device_ptr(out, "output"));
+    int64_t N = 1;
+    for (int k = 0; k < h->d; ++k) N *= h->n[k];
+    TB_TRY(check_nv(N, nv, precision == TB_PREC_C128 ? 16 : 8));
+    if (cudaSetDevice(h->device) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "cudaSetDevice"); }
+    TB_TRY(init_device_attrs(h));
+    TB_TRY(ensure_workspace(h, nv));
+    if (f0 == f1) return TB_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == TB_PREC_C128) return run_half<double>(h, half, in, out, nv, st, precision, f0, f1);
+    return run_half<float>(h, half, in, out, nv, st, precision, f0, f1);
+}
+
+}  // namespace
+
+extern "C" tb_status tb_shard_plan(int64_t nmid, int nranks, int64_t *begin, int64_t *end) {
+    if (nmid < 1 || nranks < 1 || !begin || !end) return fail(TB_EINVAL, "nmid, nranks must be positive, arrays non-NULL");
+    for (int g = 0; g < nranks; ++g) {
+        begin[g] = nmid * g / nranks;
+        end[g] = nmid * (g + 1) / nranks;
+    }
+    return TB_OK;
+}
+
+extern "C" tb_status tb_apply_src_part(tb_handle h, const void *f, void *g_mid, int64_t nv, int64_t s_begin,
+                                       int64_t s_end, int precision, void *stream) {
+    return part_common(h, 0, f, g_mid, nv, s_begin, s_end, precision, stream);
+}
+
+extern "C" tb_status tb_apply_tgt_part(tb_handle h, const void *g_mid, void *u, int64_t nv, int64_t t_begin,
+                                       int64_t t_end, int precision, void *stream) {
+    return part_common(h, 1, g_mid, u, nv, t_begin, t_end, precision, stream);
 }
 
 // ------------------------------------------------------- factor export

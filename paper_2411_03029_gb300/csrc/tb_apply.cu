@@ -213,6 +213,11 @@ __global__ void __launch_bounds__(CORE_THREADS) k_core_dense(const CoreApplyArgs
     const int64_t p = blockIdx.x / nch;
     const int64_t v0 = (int64_t)(blockIdx.x - p * nch) * a.nvc;
     const int nvc = (int)((a.nv - v0) < a.nvc ? (a.nv - v0) : a.nvc);
+    {
+        const int64_t nF = (int64_t)1 << (a.Lc * d);
+        const int64_t f = adjoint ? p / nF : p % nF;   // the pair's input-side multiset
+        if (f < a.pf0 || f >= a.pf1) return;
+    }
     int rt[MAXD], rs[MAXD];
     int Mt = 1, Ms = 1;
     for (int k = 0; k < d; ++k) {
@@ -314,6 +319,10 @@ __global__ void __launch_bounds__(CORE_THREADS, 3) k_core_rows(const CoreApplyAr
     cx<R> *Xc = reinterpret_cast<cx<R> *>(smraw);
     const int d = a.d;
     const int64_t p = blockIdx.x;
+    {
+        const int64_t f = p % ((int64_t)1 << (a.Lc * d));   // the pair's source multiset
+        if (f < a.pf0 || f >= a.pf1) return;
+    }
     int rt[MAXD], rs[MAXD];
     int Mt = 1, Ms = 1;
     for (int k = 0; k < d; ++k) {
@@ -402,6 +411,10 @@ __global__ void __launch_bounds__(CORE_THREADS, 3) k_core_regen(const CoreApplyA
     extern __shared__ __align__(16) unsigned char smraw[];
     const int d = a.d;
     const int64_t p = blockIdx.x;
+    {
+        const int64_t f = p % ((int64_t)1 << (a.Lc * d));   // the pair's source multiset
+        if (f < a.pf0 || f >= a.pf1) return;
+    }
     int rt[MAXD], rs[MAXD];
     int Mt = 1, Ms = 1;
     for (int k = 0; k < d; ++k) {

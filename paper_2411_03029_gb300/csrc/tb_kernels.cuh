@@ -143,6 +143,7 @@ struct ModeArgs {
     const cx<R> *tin;          // unit buffers of the previous / this mode
     cx<R> *tout;
     int64_t in_usize, out_usize;
+    int64_t f0, f1;            // units whose mid-level multiset F lies outside [f0, f1) are skipped
     size_t smem;
 };
 
@@ -219,6 +220,8 @@ struct CoreApplyArgs {
     int offX, offB0, offB1, offY, offA;
     size_t smem;
     CoreRegen rg;
+    int64_t pf0, pf1;      // pairs whose input-side mid-level multiset (forward: s, adjoint: t)
+                           // lies outside [pf0, pf1) are skipped
 };
 
 // Split-BF16 tensor-core core contraction (tb_core_tc.cu).  A work item is one

@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
     __shared__ const cx<R> *s_in[MODE_MAXCH];    // per child: input unit buffer / level tile
     __shared__ cx<R> *s_out[MODE_MAXCH];         // per child: output unit buffer / level tile
     __shared__ cx<R> *s_par[MODE_MAXCH];         // parent tiles by child-bit tuple (Split in, Gather out)
+    __shared__ int s_skip;                       // the unit lies outside the multiset range [f0, f1)
     const int d = a.d, k = a.k, tid = threadIdx.x;
     const bool leaf = a.pass == 0 || a.pass == 3;
     const int nchild = GROUP ? (1 << d) : 1;
@@ -163,6 +164,7 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
                 pMk[i] = (int)((pM >> ((lvl - 1) * (d - 1 - i))) & ((1 << (lvl - 1)) - 1));
         }
         const int j = tid;
+        if (j == 0) s_skip = (F < a.f0 || F >= a.f1) ? 1 : 0;
         if (j < nchild) {
             const int c = GROUP ? j : c_unit;
             int64_t M = 0;
@@ -195,6 +197,7 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
         }
     }
     __syncthreads();
+    if (s_skip) return;   // block-uniform
     for (int j = 0; j < nchild; ++j)
         stage_fac<R>(As + (int64_t)j * a.fsz, s_fac[j], a.fac.rows[k], a.fac.cols[k], a.trans != 0, a.conj != 0,
                      a.lda);
