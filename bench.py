@@ -164,33 +164,53 @@ TRAFFIC = {}
 TRAFFIC.update({("fourier6d_n16", 1, f"sep_reg@l{k}"): 1.073863e9 + 1.025651e9 for k in range(6)})
 
 
+def permode_order(d, m, o, first0=False, last_d1=False):
+    """The per-mode launch order of a pass (the library's rule): fewest complex
+    multiply-adds, mode 0 first for LeafIn / Split, mode d-1 last for Gather."""
+    import itertools
+    best, best_f = None, None
+    for p in itertools.permutations(range(d)):
+        if (first0 and p[0] != 0) or (last_d1 and p[-1] != d - 1):
+            continue
+        cur, f = list(m), 0
+        for k in p:
+            t = m[k] * o[k]
+            for j in range(d):
+                if j != k:
+                    t *= cur[j]
+            f += t
+            cur[k] = o[k]
+        if best_f is None or f < best_f:
+            best, best_f = p, f
+    return best
+
+
 def level_mode_bytes(info, w, nv, es):
     """Bytes each level pass streams as d mode-product launches: every launch
     reads its input and writes its output once (level tensors, the user tensor
-    and the mode intermediates), factors excluded."""
+    and the mode intermediates), factors excluded; each pass in its launch order."""
     d, Lc = info["d"], info["Lc"]
     P = 2 ** (2 * d * Lc)
     cb = [w.n >> info["L"]] * d
     out = {}
 
-    def chain(m, o, in_total, out_total):
+    def chain(m, o, in_total, out_total, **rule):
         b = in_total
-        for k in range(d - 1):
-            sz = P * nv * es
-            for i in range(d):
-                sz *= o[i] if i <= k else m[i]
-            b += 2 * sz
+        cur = list(m)
+        for k in permode_order(d, m, o, **rule)[:-1]:
+            cur[k] = o[k]
+            b += 2 * P * nv * es * math.prod(cur)
         return b + out_total
 
     N = w.N
     user = N * nv * es
     rs, rt = info["rank_src"], info["rank_tgt"]
     tile = lambda R: P * nv * es * math.prod(R)
-    out["leaf_in@l0"] = chain(cb, rs[0], user, tile(rs[0]))
+    out["leaf_in@l0"] = chain(cb, rs[0], user, tile(rs[0]), first0=True)
     out["leaf_out@l0"] = chain(rt[0], cb, tile(rt[0]), user)
     for l in range(1, Lc + 1):
-        out[f"split@l{l}"] = chain([2 * r for r in rs[l - 1]], rs[l], tile(rs[l - 1]), tile(rs[l]))
-        out[f"gather@l{l}"] = chain(rt[l], [2 * r for r in rt[l - 1]], tile(rt[l]), tile(rt[l - 1]))
+        out[f"split@l{l}"] = chain([2 * r for r in rs[l - 1]], rs[l], tile(rs[l - 1]), tile(rs[l]), first0=True)
+        out[f"gather@l{l}"] = chain(rt[l], [2 * r for r in rt[l - 1]], tile(rt[l]), tile(rt[l - 1]), last_d1=True)
     return out
 
 

@@ -98,6 +98,74 @@ tb_status check_nv(int64_t N, int64_t nv, size_t es) {
     return TB_OK;
 }
 
+// Complex multiply-adds per RHS of a chain X (dims m) -> Y (dims o) applied
+// in the mode order `ord`.
+double chain_cmacs_order(int d, const int *m, const int *o, const int *ord) {
+    int cur[TB_MAX_D];
+    for (int k = 0; k < d; ++k) cur[k] = m[k];
+    double f = 0.0;
+    for (int i = 0; i < d; ++i) {
+        const int k = ord[i];
+        double t = (double)m[k] * o[k];
+        for (int j = 0; j < d; ++j)
+            if (j != k) t *= cur[j];
+        f += t;
+        cur[k] = o[k];
+    }
+    return f;
+}
+
+// The mode order with the fewest multiply-adds (ties: lexicographically first).
+double best_order(int d, const int *m, const int *o, int *ord) {
+    std::vector<int> p((size_t)d);
+    for (int k = 0; k < d; ++k) p[(size_t)k] = k;
+    double best = -1.0;
+    do {
+        const double f = chain_cmacs_order(d, m, o, p.data());
+        if (best < 0.0 || f < best) {
+            best = f;
+            for (int k = 0; k < d; ++k) ord[k] = p[(size_t)k];
+        }
+    } while (std::next_permutation(p.begin(), p.end()));
+    return best;
+}
+
+// Input / output lengths of each mode of one unit of a level pass.
+void pass_dims(const tb_plan *h, Pass pass, int side, int l, int *m, int *o) {
+    const SideLevel *S = side == 0 ? h->src : h->tgt;
+    for (int k = 0; k < h->d; ++k) {
+        switch (pass) {
+            case Pass::LeafIn: m[k] = (int)h->cb[k]; o[k] = S[0].R[k]; break;
+            case Pass::LeafOut: m[k] = S[0].R[k]; o[k] = (int)h->cb[k]; break;
+            case Pass::Split: m[k] = 2 * S[l - 1].R[k]; o[k] = S[l].R[k]; break;
+            case Pass::Gather: m[k] = S[l].R[k]; o[k] = 2 * S[l - 1].R[k]; break;
+        }
+    }
+}
+
+// Mode order of a pass as per-mode launches: the fewest multiply-adds among
+// the orders the launch kinds allow (the user-tensor input of a LeafIn and the
+// parent tiles of a Split are read by mode 0 first, the parent tiles of a
+// Gather are written by mode d - 1 last; a LeafOut may end on any mode).
+void mode_order_permode(const tb_plan *h, Pass pass, int side, int l, int *ord) {
+    const int d = h->d;
+    int m[TB_MAX_D], o[TB_MAX_D];
+    pass_dims(h, pass, side, l, m, o);
+    std::vector<int> p((size_t)d);
+    for (int k = 0; k < d; ++k) p[(size_t)k] = k;
+    double best = -1.0;
+    do {
+        if ((pass == Pass::LeafIn || pass == Pass::Split) && p[0] != 0) continue;
+        if (pass == Pass::Gather && p[(size_t)d - 1] != d - 1) continue;
+        const double f = chain_cmacs_order(d, m, o, p.data());
+        if (best < 0.0 || f < best) {
+            best = f;
+            for (int k = 0; k < d; ++k) ord[k] = p[(size_t)k];
+        }
+    } while (std::next_permutation(p.begin(), p.end()));
+}
+
+
 tb_status check_device_ptr(const void *p, const char *what) {
     if (!p) return fail(TB_EINVAL, std::string(what) + " is NULL");
     cudaPointerAttributes at;
@@ -756,29 +824,28 @@ static tb_status build_sep_steps(tb_plan *h) {
 }
 
 // Largest mode intermediates (entries per RHS) of all level passes, for the
-// even and the odd modes (the two ping-pong buffers).
+// intermediates after the even and the odd launches of a pass (the two
+// ping-pong buffers), each pass in its per-mode launch order.
 static void mode_sizes(const tb_plan *h, int64_t mm[2]) {
     const int d = h->d;
     mm[0] = mm[1] = 0;
-    auto chain = [&](const int *m, const int *o) {
-        for (int k = 0; k + 1 < d; ++k) {
-            int64_t sz = h->P;
-            for (int i = 0; i < d; ++i) sz *= i <= k ? o[i] : m[i];
-            mm[k & 1] = std::max(mm[k & 1], sz);
+    const Pass passes[4] = {Pass::LeafIn, Pass::Split, Pass::Gather, Pass::LeafOut};
+    for (int side = 0; side < 2; ++side)
+        for (Pass p : passes) {
+            const bool leaf = p == Pass::LeafIn || p == Pass::LeafOut;
+            for (int l = leaf ? 0 : 1; l <= (leaf ? 0 : h->Lc); ++l) {
+                int m[TB_MAX_D], o[TB_MAX_D], ord[TB_MAX_D], cur[TB_MAX_D];
+                pass_dims(h, p, side, l, m, o);
+                mode_order_permode(h, p, side, l, ord);
+                for (int k = 0; k < d; ++k) cur[k] = m[k];
+                for (int st = 0; st + 1 < d; ++st) {
+                    cur[ord[st]] = o[ord[st]];
+                    int64_t sz = h->P;
+                    for (int k = 0; k < d; ++k) sz *= cur[k];
+                    mm[st & 1] = std::max(mm[st & 1], sz);
+                }
+            }
         }
-    };
-    for (int side = 0; side < 2; ++side) {
-        const SideLevel *S = side == 0 ? h->src : h->tgt;
-        int m[TB_MAX_D], o[TB_MAX_D];
-        for (int k = 0; k < d; ++k) { m[k] = (int)h->cb[k]; o[k] = S[0].R[k]; }
-        chain(m, o);
-        chain(o, m);
-        for (int l = 1; l <= h->Lc; ++l) {
-            for (int k = 0; k < d; ++k) { m[k] = 2 * S[l - 1].R[k]; o[k] = S[l].R[k]; }
-            chain(m, o);
-            chain(o, m);
-        }
-    }
 }
 
 // Whether the cores can be regenerated inside the contraction with exact
@@ -1153,6 +1220,7 @@ int mode_ob_rule(int o) {
     return ob;
 }
 
+
 // One level pass as d mode-product launches (tb_mode.cu).  T holds the two
 // ping-pong buffers of the mode intermediates.
 template <class R>
@@ -1216,18 +1284,27 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
     int64_t gtab = 0;
     for (int k = 0; k < d; ++k) gtab += h->cb[k];
     const tb::ModeTune *tune = h->tune[std::is_same<R, double>::value ? 1 : 0][side][(int)pass][leaf ? 0 : l];
-    for (int k = 0; k < d; ++k) {
-        if (only_k >= 0 && k != only_k) continue;
+    int ord[TB_MAX_D];
+    mode_order_permode(h, pass, side, l, ord);
+    int cur[TB_MAX_D];
+    for (int i = 0; i < d; ++i) cur[i] = m[i];
+    for (int step = 0; step < d; ++step) {
+        const int k = ord[step];
+        if (only_k >= 0 && k != only_k) {
+            cur[k] = o[k];
+            continue;
+        }
         a.k = k;
         a.m = m[k];
         a.o = o[k];
         int64_t pre = 1, post = nv, usz_in = nv, usz_out = nv;
-        for (int i = 0; i < k; ++i) pre *= o[i];
-        for (int i = k + 1; i < d; ++i) post *= m[i];
+        for (int i = 0; i < k; ++i) pre *= cur[i];
+        for (int i = k + 1; i < d; ++i) post *= cur[i];
         for (int i = 0; i < d; ++i) {
-            usz_in *= i < k ? o[i] : m[i];
-            usz_out *= i <= k ? o[i] : m[i];
+            usz_in *= cur[i];
+            usz_out *= i == k ? o[i] : cur[i];
         }
+        cur[k] = o[k];
         a.pre = pre;
         a.post = post;
         a.cols = pre * post;
@@ -1236,20 +1313,20 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
         a.out_tile = 0;
         a.tin = nullptr;
         a.tout = nullptr;
-        if (k == 0) {
+        if (step == 0) {
             if (pass == Pass::LeafIn) ink = MK_USER;
             else if (pass == Pass::Split) ink = MK_PARENTS;
             else a.in_tile = 1;
         } else {
-            a.tin = (const cx<R> *)T[(k - 1) & 1];
+            a.tin = (const cx<R> *)T[(step - 1) & 1];
             a.in_usize = usz_in;
         }
-        if (k == d - 1) {
+        if (step == d - 1) {
             if (pass == Pass::LeafOut) outk = MK_USER;
             else if (pass == Pass::Gather) outk = MK_PARENTS;
             else a.out_tile = 1;
         } else {
-            a.tout = (cx<R> *)T[k & 1];
+            a.tout = (cx<R> *)T[step & 1];
             a.out_usize = usz_out;
         }
         const bool group = ink == MK_PARENTS || outk == MK_PARENTS;
@@ -1277,50 +1354,8 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
     return TB_OK;
 }
 
-// Complex multiply-adds per RHS of a chain X (dims m) -> Y (dims o) applied
-// in the mode order `ord`.
-double chain_cmacs_order(int d, const int *m, const int *o, const int *ord) {
-    int cur[TB_MAX_D];
-    for (int k = 0; k < d; ++k) cur[k] = m[k];
-    double f = 0.0;
-    for (int i = 0; i < d; ++i) {
-        const int k = ord[i];
-        double t = (double)m[k] * o[k];
-        for (int j = 0; j < d; ++j)
-            if (j != k) t *= cur[j];
-        f += t;
-        cur[k] = o[k];
-    }
-    return f;
-}
 
-// The mode order with the fewest multiply-adds (ties: lexicographically first).
-double best_order(int d, const int *m, const int *o, int *ord) {
-    std::vector<int> p((size_t)d);
-    for (int k = 0; k < d; ++k) p[(size_t)k] = k;
-    double best = -1.0;
-    do {
-        const double f = chain_cmacs_order(d, m, o, p.data());
-        if (best < 0.0 || f < best) {
-            best = f;
-            for (int k = 0; k < d; ++k) ord[k] = p[(size_t)k];
-        }
-    } while (std::next_permutation(p.begin(), p.end()));
-    return best;
-}
 
-// Input / output lengths of each mode of one unit of a level pass.
-void pass_dims(const tb_plan *h, Pass pass, int side, int l, int *m, int *o) {
-    const SideLevel *S = side == 0 ? h->src : h->tgt;
-    for (int k = 0; k < h->d; ++k) {
-        switch (pass) {
-            case Pass::LeafIn: m[k] = (int)h->cb[k]; o[k] = S[0].R[k]; break;
-            case Pass::LeafOut: m[k] = S[0].R[k]; o[k] = (int)h->cb[k]; break;
-            case Pass::Split: m[k] = 2 * S[l - 1].R[k]; o[k] = S[l].R[k]; break;
-            case Pass::Gather: m[k] = S[l].R[k]; o[k] = 2 * S[l - 1].R[k]; break;
-        }
-    }
-}
 
 // Whether a level pass runs fused: tb_options.level_schedule, then the tuner's
 // per-pass choice (the faster of the two forms), then the built-in rule

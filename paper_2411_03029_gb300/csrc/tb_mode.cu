@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
     cx<R> *yp0[NC], *yp1[NC];
     int rpl = 0;
     int64_t gslnv = 0;
-    const int *gtl = gt + goff[d - 1];
+    const int *gtl = gt + goff[k];   // tree order of the last mode (LeafOut)
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
         yoff[j] = pcol[j] * o * post + qcol[j];
@@ -286,15 +286,24 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
             yp0[j] = s_par[bits] + (int64_t)erest * nv + qcol[j];
             yp1[j] = s_par[bits | 1] + (int64_t)erest * nv + qcol[j];
         } else if (OUT == MK_USER) {
+            // the last mode k of a LeafOut: every other mode is already at its leaf
+            // size; p runs over the modes before k, q over the modes after k and v
             int rem = pcol[j];
             int64_t ub = 0;
-            for (int i = d - 2; i >= 0; --i) {
+            for (int i = k - 1; i >= 0; --i) {
                 const int ai = rem % a.cb[i];
                 rem /= a.cb[i];
                 ub += (int64_t)gt[goff[i] + ai] * a.user.gstride[i];
             }
-            yp0[j] = a.user.p + ub * nv + qcol[j];
-            gslnv = a.user.gstride[d - 1] * (int64_t)nv;
+            int remq = qcol[j] / nv;
+            const int v = qcol[j] - remq * nv;
+            for (int i = d - 1; i > k; --i) {
+                const int ai = remq % a.cb[i];
+                remq /= a.cb[i];
+                ub += (int64_t)gt[goff[i] + ai] * a.user.gstride[i];
+            }
+            yp0[j] = a.user.p + ub * nv + v;
+            gslnv = a.user.gstride[k] * (int64_t)nv;
         }
     }
 
