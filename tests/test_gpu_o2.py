@@ -73,7 +73,7 @@ CASES = {
     "helmholtz3d": W.small("helmholtz3d_n64", 16, nv=3, L=2),
     "radon2d": W.small("radon2d_n256", 64, nv=3, L=4),
     "helmholtz3d_n32_bf16": W.small("helmholtz3d_n256", 32, nv=16, L=2, params=(2 * np.pi * 8,)),
-    # one RHS: the forward core takes its one-RHS kernel (32 rows per warp)
+    # one RHS: the forward core takes its one-RHS kernel (16 rows per warp)
     "helmholtz3d_nv1": W.small("helmholtz3d_n64", 32, nv=1, L=2),
 }
 
