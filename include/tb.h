@@ -70,8 +70,11 @@ typedef enum {
 typedef enum {
     TB_PREC_C128 = 0,          /* complex128 data, FP64 arithmetic ("plain FP64") */
     TB_PREC_C64 = 1,           /* complex64 data, FP32 arithmetic */
-    TB_PREC_C64_SPLITBF16 = 2  /* complex64 data; mid-level cores as two-term split
-                                  BF16 on the tensor cores with FP32 accumulation */
+    TB_PREC_C64_SPLITBF16 = 2  /* complex64 data; the contractions on the tcgen05 tensor
+                                  cores in two-term split BF16 (hi = rn(v), lo = rn(v - hi))
+                                  with FP32 accumulation: the mid-level cores and, where
+                                  the level passes run on the tensor cores
+                                  (tb_options.level_schedule), the mode products */
 } tb_precision;
 
 typedef enum {
@@ -117,12 +120,17 @@ typedef struct {
                               5 = as 3 with scalar FMAs, one fiber per thread and the
                                   next fiber's loads in flight,
                               6 = as 3 with one fiber per thread (4 resident blocks per SM) */
-    int level_schedule;    /* non-separable level passes (Alg. 2 steps 1 and 3), complex64:
-                              0 = built-in rule (= 2 where it applies: d <= 3),
-                              1 = d launches per pass, one per mode product,
-                              2 = one fused persistent launch per pass (the mode products
-                                  of a unit back to back, intermediates in a per-block
-                                  scratch); complex128 always uses 1 */
+    int level_schedule;    /* non-separable level passes (Alg. 2 steps 1 and 3), complex64 data:
+                              0 = built-in rule: 1; tb_autotune may pick another form per pass
+                                  (3 only for split-BF16 applies),
+                              1 = d launches per pass, one per mode product (FP32 FMAs),
+                              2 = one fused persistent launch per pass on the CUDA cores (the
+                                  mode products of a unit back to back, intermediates in
+                                  shared memory),
+                              3 = one persistent launch per pass on the tcgen05 tensor cores:
+                                  each mode product in two-term split BF16 with FP32
+                                  accumulation (split-BF16 applies; the others use 1);
+                              complex128 always uses 1 */
     int core_mode;         /* the forward complex64 mid-level core with one RHS (Alg. 2 step 2):
                               0 = built-in rule (stored cores; tb_autotune may pick 2),
                               1 = read the stored cores K(t-bar, s-bar),

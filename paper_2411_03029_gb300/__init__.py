@@ -24,7 +24,7 @@ TB_MAX_LEVELS = 16
 KERNEL_FOURIER, KERNEL_HELMHOLTZ, KERNEL_RADON, KERNEL_RADON_ANISO = 1, 2, 3, 4
 PREC_C128, PREC_C64, PREC_C64_SPLITBF16 = 0, 1, 2
 SEP_RULE, SEP_FIBER, SEP_TILE, SEP_REGISTER, SEP_REGISTER_PAIRS, SEP_REGISTER_SCALAR, SEP_REGISTER_ONE = range(7)
-LEVEL_RULE, LEVEL_PER_MODE, LEVEL_FUSED = range(3)
+LEVEL_RULE, LEVEL_PER_MODE, LEVEL_FUSED, LEVEL_TENSOR = range(4)
 CORE_RULE, CORE_STORED, CORE_REGENERATE = range(3)
 ORDER_AUTO, ORDER_NATURAL, ORDER_BITREV = -1, 0, 1
 

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "tb_kernels.cuh"
+#include "tb_tc.cuh"
 #include "tb_plan.cuh"
 
 using namespace tb;
@@ -1029,7 +1030,7 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     if (L % 2 != 0 || L < 0 || L >= TB_MAX_LEVELS || (nmin >> L) < 1)
         return fail(TB_EINVAL, "L must be even with n_k / 2^L >= 1");
     if (opt.sep_schedule < 0 || opt.sep_schedule > 6) return fail(TB_EINVAL, "sep_schedule must be in [0, 6]");
-    if (opt.level_schedule < 0 || opt.level_schedule > 2) return fail(TB_EINVAL, "level_schedule must be in [0, 2]");
+    if (opt.level_schedule < 0 || opt.level_schedule > 3) return fail(TB_EINVAL, "level_schedule must be in [0, 3]");
     if (opt.core_mode < 0 || opt.core_mode > 2) return fail(TB_EINVAL, "core_mode must be in [0, 2]");
     int dev = opt.device;
     if (dev < 0) {
@@ -1361,24 +1362,34 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
 // per-pass choice (the faster of the two forms), then the built-in rule
 // (per-mode launches).
 bool level_fused_wanted(const tb_plan *h, Pass pass, int side, int l) {
-    if (h->level_choice == 1) return false;
+    if (h->level_choice == 1 || h->level_choice == 3) return false;
     if (h->level_choice == 2) return true;
     const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
     return h->ltune[side][(int)pass][leaf ? 0 : l].mode == 2;
+}
+
+// Whether a level pass runs on the tensor cores (split-BF16 applies only):
+// tb_options.level_schedule = 3, else the tuner's per-pass choice (the
+// built-in rule keeps the per-mode launches, measured faster at the
+// benchmark ranks).
+bool level_tc_wanted(const tb_plan *h, Pass pass, int side, int l, int precision) {
+    if (precision != TB_PREC_C64_SPLITBF16) return false;
+    if (h->level_choice == 3) return true;
+    if (h->level_choice != 0) return false;
+    const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
+    return h->ltune[side][(int)pass][leaf ? 0 : l].mode == 3;
 }
 
 // One level pass as a single fused persistent launch (k_level, complex64),
 // its intermediates in `scratch` (scratch_bytes long).  done = false (and
 // nothing launched) when the pass does not fit the fused kernel: d > 3, too
 // little scratch or shared memory.  dry = true only plans.
-tb_status level_pass_fused(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out,
-                           int64_t nv, cudaStream_t st, void *scratch, size_t scratch_bytes, bool &done,
-                           bool dry = false, int vc_set = 0, int cps_set = 0, int obmax_set = 0) {
-    done = false;
+// The pass-generic part of a fused level launch's arguments: dims, item
+// decomposition, tiles, factors and the user tensor.
+void level_args_common(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out,
+                       int64_t nv, LevelArgs &a) {
     const int d = h->d, Lc = h->Lc;
-    if (d > 3 || (1 << d) > level_max_children()) return TB_OK;
     const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
-    LevelArgs a;
     std::memset(&a, 0, sizeof(a));
     a.d = d;
     a.Lc = Lc;
@@ -1427,6 +1438,20 @@ tb_status level_pass_fused(const tb_plan *h, Pass pass, bool conj, int side, int
     }
     a.lvl = leaf ? 0 : l;
     a.lgs = Lc - a.lvl;
+    for (int k = 0; k < d; ++k) a.lcb[k] = ilog2(h->cb[k]);
+}
+
+tb_status level_pass_fused(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out,
+                           int64_t nv, cudaStream_t st, void *scratch, size_t scratch_bytes, bool &done,
+                           bool dry = false, int vc_set = 0, int cps_set = 0, int obmax_set = 0) {
+    done = false;
+    const int d = h->d, Lc = h->Lc;
+    if (d > 3 || (1 << d) > level_max_children()) return TB_OK;
+    const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
+    LevelArgs a;
+    level_args_common(h, pass, conj, side, l, in, out, nv, a);
+    int m[TB_MAX_D], o[TB_MAX_D];
+    pass_dims(h, pass, side, l, m, o);
     best_order(d, m, o, a.order);
     const tb::LevelTune &tn = h->ltune[side][(int)pass][leaf ? 0 : l];
     // output rows per register chunk, one value for the launch: the even value
@@ -1522,6 +1547,195 @@ tb_status level_pass_fused(const tb_plan *h, Pass pass, bool conj, int side, int
     TB_CK(launch_level(a, OB, (int)blocks, st));
     return TB_OK;
 }
+
+// ------------------------------------------- level passes on the tensor cores
+// Plan of a level pass for k_level_tc with vc RHS per work item and mode order
+// ord: per-step operand shapes, shared-memory layout and accumulator columns.
+// Bit i of rowbits swaps the order of step i's two other modes (d = 3) in its
+// operand rows; the cost counts the shared-memory wavefronts of one warp's
+// accumulator stores into the next operand (simulated here).
+// false when it does not fit (shared memory, tensor memory, MMA N <= 256).
+bool plan_level_tc(const tb_plan *h, Pass pass, int vc, const int *ord, int rowbits, LevelTcArgs &A,
+                   double *cost) {
+    const int d = h->d;
+    LevelArgs &a = A.L;
+    const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
+    const bool split = pass == Pass::Split, gather = pass == Pass::Gather;
+    std::memset(A.st, 0, sizeof(A.st));
+    int cur[LTC_MAXD];
+    for (int k = 0; k < d; ++k) cur[k] = a.m[k];
+    double c = 0.0;
+    uint32_t abytes_max = 0, a0_bytes = 0, bbytes = 0, cols_max = 0;
+    auto up = [](uint32_t x, uint32_t al) { return (x + al - 1) / al * al; };
+    for (int i = 0; i < d; ++i) {
+        LtcStep &S = A.st[i];
+        const int k = ord[i];
+        S.k = k;
+        S.m = cur[k];
+        S.o = a.o[k];
+        if (2 * S.o > 256 || S.m > 128) return false;   // MMA N <= 256
+        if (i == 0 && S.m > 32) return false;             // the staging holds a fiber of <= 32
+        // the other modes in C order, the two swapped where rowbits says so
+        S.nod = 0;
+        int64_t rows = vc;
+        for (int j = 0; j < d; ++j)
+            if (j != k) {
+                S.om[S.nod] = j;
+                S.od[S.nod] = cur[j];
+                ++S.nod;
+            }
+        if (S.nod == 2 && ((rowbits >> i) & 1)) {
+            std::swap(S.om[0], S.om[1]);
+            std::swap(S.od[0], S.od[1]);
+        }
+        for (int jj = 0; jj < S.nod; ++jj) rows *= S.od[jj];
+        int st = vc;
+        for (int jj = S.nod - 1; jj >= 0; --jj) {
+            S.rstr[S.om[jj]] = st;
+            st *= S.od[jj];
+        }
+        S.rstr[k] = 0;
+        if (rows > (1 << 20)) return false;
+        S.rows = (int)rows;
+        S.tiles = (S.rows + 127) / 128;
+        S.ks = (S.m + 3) / 4;                  // 4 complex (hi, lo interleaved) per K-step
+        S.np = (2 * S.o + 15) / 16 * 16;
+        S.a_rs = (uint32_t)S.tiles * 4096u;
+        S.b_rs = (uint32_t)S.np * 32u;
+        S.b_half = (uint32_t)S.ks * S.b_rs;    // B1, then B2
+        S.b_off = bbytes;
+        bbytes += up(2 * S.b_half, 1024);
+        S.idesc = tc::idesc_bf16(S.np);
+        const uint32_t ab = (uint32_t)S.ks * S.a_rs;
+        if (i == 0 && split) a0_bytes = ab;
+        else abytes_max = std::max(abytes_max, ab);
+        const uint32_t cols = (uint32_t)S.tiles * S.np;
+        if (!(gather && i == d - 1)) cols_max = std::max(cols_max, cols);
+        // tensor-pipe cycles (2 MMAs of N / 2 cycles per tile and K-step) plus
+        // the conversion of the accumulator (about 10 instructions per output)
+        c += 1.0 * S.tiles * S.ks * S.np + 0.08 * (double)S.rows * S.o;
+        cur[k] = a.o[k];
+    }
+    {
+        LtcStep &S = A.st[d - 1];
+        int st = 1;
+        for (int j = d - 1; j >= 0; --j) {
+            S.tstr[j] = st;
+            st *= a.o[j];
+        }
+        if (gather) {
+            S.tcol = (cols_max + 31) / 32 * 32;
+            if (S.tcol + (uint32_t)S.tiles * S.np > 256) return false;
+        }
+    }
+    if (cols_max > 256) return false;
+    // shared memory: [split: step-0 operand] [warpgroup 0] [warpgroup 1] [slack]
+    int64_t gtab = 0;
+    for (int k = 0; k < d; ++k) gtab += h->cb[k];
+    const uint32_t tab = leaf ? up((uint32_t)gtab * 12u, 16) : 0;
+    A.fac_off = up(abytes_max, 1024);
+    A.tab_off = A.fac_off + bbytes;
+    const uint32_t wg_bytes = up(A.tab_off + tab, 1024);
+    uint32_t off = 0;
+    A.a0_off = 0;
+    if (split) off = up(a0_bytes, 1024);
+    A.wg_off[0] = off;
+    A.wg_off[1] = off + wg_bytes;
+    // 1 KB for the base alignment and 2 KB of slack past the last operand
+    uint32_t smem = off + 2 * wg_bytes + 1024 + 2048;
+    const uint32_t budget = (uint32_t)g_smem_optin - 2048;   // static shared arrays
+    if (smem > budget) return false;
+    // one block per SM (it holds all 512 tensor-memory columns)
+    smem = std::max<uint32_t>(smem, (uint32_t)g_smem_optin / 2 + 4096);
+    A.smem = std::min(smem, budget);
+    // shared-memory wavefronts of the accumulator stores of warp 0, tile 0
+    // (output 0) into the next operand: 8-byte stores, 16 slots per wavefront
+    for (int i = 0; i + 1 < d; ++i) {
+        const LtcStep &S = A.st[i], &N = A.st[i + 1];
+        int cnt[16] = {0};
+        for (int r = 0; r < 32 && r < S.rows; ++r) {
+            int idx[LTC_MAXD] = {0, 0, 0};
+            int rest = r / vc;
+            for (int jj = S.nod - 1; jj >= 0; --jj) {
+                idx[S.om[jj]] = rest % S.od[jj];
+                rest /= S.od[jj];
+            }
+            int rr = r % vc;
+            for (int j = 0; j < d; ++j)
+                if (j != S.k) rr += idx[j] * N.rstr[j];
+            const int kp = idx[N.k];
+            const uint32_t off = (uint32_t)(kp >> 2) * N.a_rs + tc::sw32c((uint32_t)rr, (uint32_t)(kp & 3));
+            ++cnt[(off >> 3) & 15];
+        }
+        int deg = 1;
+        for (int u = 0; u < 16; ++u) deg = std::max(deg, cnt[u]);
+        c += 0.04 * (double)S.rows * S.o * deg;
+    }
+    if (cost) *cost = c;
+    return true;
+}
+
+// One level pass as a single persistent launch on the tensor cores
+// (k_level_tc, complex64 data, split-BF16 products).  done = false (nothing
+// launched) when the pass does not fit the kernel.  dry = true only plans.
+tb_status level_pass_tc(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out,
+                        int64_t nv, cudaStream_t st, bool &done, bool dry = false, int vc_set = 0) {
+    done = false;
+    const int d = h->d;
+    if (d > LTC_MAXD || d < 1) return TB_OK;
+    const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
+    LevelTcArgs A;
+    std::memset(&A, 0, sizeof(A));
+    level_args_common(h, pass, conj, side, l, in, out, nv, A.L);
+    LevelArgs &a = A.L;
+    A.err = h->d_err;
+    const tb::LevelTune &tn = h->ltune[side][(int)pass][leaf ? 0 : l];
+    int vc = vc_set ? vc_set : tn.tc_vc;
+    int cands[3] = {4, 2, 1}, nc = 3;
+    if (vc > 0) {
+        cands[0] = vc;
+        nc = 1;
+    }
+    bool found = false;
+    for (int ci = 0; ci < nc && !found; ++ci) {
+        int v = (int)std::min<int64_t>(cands[ci], nv);
+        while (v & (v - 1)) --v;
+        // the mode order with the lowest planned cost among those that fit
+        std::vector<int> p((size_t)d);
+        for (int k = 0; k < d; ++k) p[(size_t)k] = k;
+        double best = -1.0;
+        int bord[LTC_MAXD] = {0, 1, 2};
+        int brow = 0;
+        do {
+            for (int rb = 0; rb < (1 << d); ++rb) {
+                double c = 0.0;
+                if (!plan_level_tc(h, pass, v, p.data(), rb, A, &c)) continue;
+                if (best < 0.0 || c < best) {
+                    best = c;
+                    brow = rb;
+                    for (int k = 0; k < d; ++k) bord[k] = p[(size_t)k];
+                }
+            }
+        } while (std::next_permutation(p.begin(), p.end()));
+        if (best < 0.0) continue;
+        a.vc = v;
+        plan_level_tc(h, pass, v, bord, brow, A, nullptr);
+        for (int k = 0; k < d; ++k) a.order[k] = bord[k];
+        found = true;
+    }
+    if (!found) return TB_OK;
+    a.lvc = ilog2(a.vc);
+    a.nq = (int)((nv + a.vc - 1) / a.vc);
+    const int64_t nunits = leaf ? h->P : (h->P >> d);
+    a.nitems = nunits * a.nq;
+    const int64_t per = leaf ? 2 : 1;   // work items per block at a time
+    const int64_t blocks = std::min<int64_t>((a.nitems + per - 1) / per, (int64_t)g_num_sms);
+    done = true;
+    if (dry) return TB_OK;
+    TB_CK(launch_level_tc(A, (int)blocks, st));
+    return TB_OK;
+}
+
 
 template <class R>
 const cx<R> *coreptr(const tb_plan *h);
@@ -1938,6 +2152,15 @@ tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t
         int64_t bytes = 0;
         double flops = 0;
         if (prof) pass_cost(h, p, side, l, nv, es, bytes, flops);
+        if (std::is_same<R, float>::value && level_tc_wanted(h, p, side, l, precision)) {
+            bool ok = false;
+            TB_TRY(level_pass_tc(h, p, adjoint, side, l, i, o, nv, st, ok, true));
+            if (ok)
+                return timed(name, l, bytes, flops, 1, [&] {
+                    bool done = false;
+                    return level_pass_tc(h, p, adjoint, side, l, i, o, nv, st, done);
+                });
+        }
         if (std::is_same<R, float>::value && h->level_choice != 1 && level_fused_wanted(h, p, side, l)) {
             bool ok = false;
             TB_TRY(level_pass_fused(h, p, adjoint, side, l, i, o, nv, st, T[0], T0bytes, ok, true));
@@ -2123,7 +2346,29 @@ tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, cons
                                         best.obmax = ob;
                                     }
                                 }
-                        if (best.mode == 2 && h->level_choice == 0) {
+                        // split-BF16 applies: the tensor-core launch, RHS per work item
+                        if (status == TB_OK && precision == TB_PREC_C64_SPLITBF16 &&
+                            (h->level_choice == 0 || h->level_choice == 3)) {
+                            for (int vc : {1, 2, 4}) {
+                                bool ok = false;
+                                status = level_pass_tc(h, p, false, side, l, in, out, nv, st, ok, true, vc);
+                                if (status != TB_OK || !ok) continue;
+                                float t = 0.f;
+                                status = time_it(
+                                    [&] {
+                                        bool done = false;
+                                        return level_pass_tc(h, p, false, side, l, in, out, nv, st, done, false, vc);
+                                    },
+                                    t);
+                                if (status != TB_OK) break;
+                                if (t < tbest) {
+                                    tbest = t;
+                                    best.mode = 3;
+                                    best.tc_vc = vc;
+                                }
+                            }
+                        }
+                        if (status == TB_OK && best.mode >= 2 && h->level_choice == 0) {
                             // against the per-mode launches of the same pass (their shapes
                             // as tuned below are not known yet: the built-in ones)
                             float tmode = 3.0e38f;

@@ -184,6 +184,37 @@ bool level_ob_valid(int ob);
 int level_threads();
 int level_max_children();
 
+// A level pass as one persistent launch on the tcgen05 tensor cores
+// (k_level_tc, split-BF16 mode products, FP32 accumulation; d <= 3).  Step i
+// of a chain is the mode product of mode k = st[i].k, a tensor-core product
+// D = X B^T with X the step's operand (rows = the entries of the other modes
+// times the item's vc RHS, K = the m complex inputs of mode k, each as
+// (hi re, hi im, lo re, lo im)) and B1, B2 the split real forms of the op(A)
+// block (rows 2 o', 2 o' + 1).
+constexpr int LTC_MAXD = 3;
+struct LtcStep {
+    int k, m, o;                   // mode, input / output length
+    int rows, tiles, ks, np;       // operand rows, 128-row tiles, K-steps of 4 complex, MMA N (>= 2 o)
+    int nod, om[LTC_MAXD], od[LTC_MAXD];   // the other modes, slowest first, and their current lengths
+    int rstr[LTC_MAXD];            // row stride of each mode in this step's operand (0 for mode k)
+    int tstr[LTC_MAXD];            // last step: entry stride of each mode in the output tile
+    uint32_t a_rs;                 // operand: K-step region stride (tiles x 4 KB)
+    uint32_t b_off, b_rs, b_half;  // B1 at b_off in the warpgroup's factor area, B2 b_half later
+    uint32_t tcol;                 // accumulator column of tile 0
+    uint32_t idesc;
+};
+struct LevelTcArgs {
+    LevelArgs L;                   // pass, dims, item decomposition, tiles, factors, user tensor
+    LtcStep st[LTC_MAXD];
+    uint32_t a0_off;               // Split: the step-0 operand shared by the block
+    uint32_t wg_off[2];            // per warpgroup: operand buffer, then factors, then leaf tables
+    uint32_t fac_off, tab_off;     // offsets within a warpgroup's area
+    uint32_t smem;
+    int *err;                      // device error word (TB_ETIMEOUT)
+};
+cudaError_t launch_level_tc(const LevelTcArgs &a, int blocks, cudaStream_t st);
+int level_tc_threads();
+
 // Regeneration of the mid-level cores K(t-bar, s-bar) from the skeleton points
 // inside the one-RHS forward core (k_core_regen), for the kernels whose
 // distances or phases are exact integers on uniform grids:

@@ -61,10 +61,12 @@ struct ProfRec {
 // Launch shape of one fused level pass picked by tb_autotune (0 = the
 // built-in rule).
 struct LevelTune {
-    int mode = 0;    // 1 = the per-mode launches won the tuning, 2 = the fused launch
+    int mode = 0;    // 1 = the per-mode launches won the tuning, 2 = the fused launch,
+                     // 3 = the tensor-core launch (split-BF16 applies)
     int vc = 0;      // right-hand sides per work item
     int cps = 0;     // resident thread blocks per SM the grid is sized for
     int obmax = 0;   // largest register chunk of output rows (4 .. 16)
+    int tc_vc = 0;   // right-hand sides per work item of the tensor-core launch
 };
 
 // Launch shape of one mode-product launch picked by tb_autotune (0 = the

@@ -63,6 +63,8 @@ def test_fourier_bitrev_is_exact(d, n, L, separable):
         # exact ranks: the butterfly itself is exact, so what remains is the
         # rounding of the split-BF16 core (two BF16 terms per value and per core
         # entry, about 16 bits, FP32 accumulation) plus the FP32 level passes
+        # (the per-mode launches, so that the core is pinned on its own)
+        op = tb.from_workload(w, separable=separable, level_schedule=tb.LEVEL_PER_MODE)
         ubf = run(op, w, f, tb.PREC_C64_SPLITBF16)
         assert rel(ubf, ref) < 5e-5, rel(ubf, ref)
         vbf = run(op, w, f, tb.PREC_C64_SPLITBF16, adjoint=True)
@@ -207,7 +209,8 @@ def test_splitbf16_core_matches_c64_and_oracle(nv):
     # within the workload bound (1e-3 at eps = 1e-4) against the oracle
     # 4 points per wavelength, as in the n = 256 workload
     w = W.small("helmholtz3d_n256", 32, nv=nv, L=2, params=(2 * np.pi * 8,))
-    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C64_SPLITBF16))
+    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C64_SPLITBF16),
+                          level_schedule=tb.LEVEL_PER_MODE)
     f = W.rhs(w)
     u32 = run(op, w, f, tb.PREC_C64)
     ubf = run(op, w, f, tb.PREC_C64_SPLITBF16)
@@ -222,7 +225,8 @@ def test_splitbf16_core_matches_c64_and_oracle(nv):
 
 def test_splitbf16_core_multilevel_and_deterministic():
     w = W.small("helmholtz3d_n256", 64, nv=16, L=4, params=(2 * np.pi * 16,))
-    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C64_SPLITBF16))
+    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C64_SPLITBF16),
+                          level_schedule=tb.LEVEL_PER_MODE)
     f = W.rhs(w)
     rows = W.sample_targets(w, 512)
     ubf = run(op, w, f, tb.PREC_C64_SPLITBF16)
