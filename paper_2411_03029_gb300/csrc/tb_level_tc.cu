@@ -30,13 +30,12 @@
 // warpgroup's mbarrier, and the 128 threads (thread = TMEM lane = operand row)
 // read the accumulator and write the next step's operand, split into BF16
 // pairs, into the same buffer (the step's MMAs have completed).  The other
-// warpgroup's work overlaps each wait.
+// warpgroup's work overlaps each wait.  The rows of a step's operand
+// enumerate its other modes in an order the host picks per step (the one
+// whose 8-byte accumulator stores into the next operand, simulated for one
+// warp, take the fewest shared-memory wavefronts).
 //  * LeafIn / LeafOut: each warpgroup takes its own work items (a leaf tile
 //    and a chunk of vc RHS).
-// The rows of a step's operand enumerate its other modes with the next step's
-// mode slowest, so the 32 lanes of a warp (consecutive rows) write
-// consecutive rows of the next operand: 8-byte stores, at most two-way bank
-// conflicts.
 //  * Split: the block takes an item (a group of 2^d children, vc RHS) and
 //    stages the combined parent tile once as the step-0 operand shared by
 //    both warpgroups; warpgroup g runs children g, g + 2, ...
