@@ -145,9 +145,10 @@ void pass_dims(const tb_plan *h, Pass pass, int side, int l, int *m, int *o) {
 }
 
 // Mode order of a pass as per-mode launches: the fewest multiply-adds among
-// the orders the launch kinds allow (the user-tensor input of a LeafIn and the
-// parent tiles of a Split are read by mode 0 first, the parent tiles of a
-// Gather are written by mode d - 1 last; a LeafOut may end on any mode).
+// the orders the launch kinds allow (the user-tensor input of a LeafIn is
+// read by mode 0 first, as are the parent tiles of a Split, the parent tiles of
+// a Gather are written by mode d - 1 last; a LeafOut may end on any mode).
+// Among orders of equal cost the lexicographically last is taken.
 void mode_order_permode(const tb_plan *h, Pass pass, int side, int l, int *ord) {
     const int d = h->d;
     int m[TB_MAX_D], o[TB_MAX_D];
@@ -159,7 +160,7 @@ void mode_order_permode(const tb_plan *h, Pass pass, int side, int l, int *ord) 
         if ((pass == Pass::LeafIn || pass == Pass::Split) && p[0] != 0) continue;
         if (pass == Pass::Gather && p[(size_t)d - 1] != d - 1) continue;
         const double f = chain_cmacs_order(d, m, o, p.data());
-        if (best < 0.0 || f < best) {
+        if (best < 0.0 || f <= best) {   // ties: the last order
             best = f;
             for (int k = 0; k < d; ++k) ord[k] = p[(size_t)k];
         }
