@@ -53,6 +53,7 @@ def parse():
                         "3-D Helmholtz configuration when they apply; else the live oracle, capped)")
     p.add_argument("--profile-only", action="store_true", help="eager applies only (for ncu)")
     p.add_argument("--n", type=int, default=None, help="points per axis of a reduced-size copy (profiling)")
+    p.add_argument("--nv", type=int, default=None, help="right-hand sides of a reduced-size copy (profiling)")
     p.add_argument("--level-schedule", type=int, default=0,
                    help="non-separable handles: tb_options.level_schedule (0 rule, 1 per-mode, 2 fused)")
     p.add_argument("--core-mode", type=int, default=0,
@@ -64,12 +65,13 @@ def parse():
 
 def workload(args):
     w = W.WORKLOADS[args.workload]
-    if not args.n:
+    if not args.n and not args.nv:
         return w
+    n = args.n or w.n
     kw = {}
-    if w.kind == W.HELMHOLTZ:   # keep the points per wavelength of the full workload
-        kw["params"] = (w.params[0] * args.n / w.n,)
-    return W.small(args.workload, args.n, nv=w.nv, **kw)
+    if w.kind == W.HELMHOLTZ and n != w.n:   # keep the points per wavelength of the full workload
+        kw["params"] = (w.params[0] * n / w.n,)
+    return W.small(args.workload, n, nv=args.nv or w.nv, **kw)
 
 
 def dist_init():
