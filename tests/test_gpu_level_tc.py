@@ -81,7 +81,7 @@ def test_tensor_core_level_passes_match_fp32_per_mode_launches(name, w):
     tc.close()
 
 
-@pytest.mark.parametrize("d,n,L", [(2, 16, 2), (2, 64, 4), (3, 16, 2), (3, 32, 2)])
+@pytest.mark.parametrize("d,n,L", [(1, 64, 4), (2, 16, 2), (2, 64, 4), (3, 16, 2), (3, 32, 2)])
 def test_tensor_core_levels_on_the_exact_dft_butterfly(d, n, L):
     # bit-reversed uniform DFT: every block has exact rank C_b, so the butterfly
     # is exact and what remains is the split-BF16 rounding of the chain
