@@ -163,7 +163,7 @@ class ClockSampler:
 # the kernel changes.
 TRAFFIC = {}
 # k_core_tc, one launch of helmholtz3d_n256 (16 RHS): ncu dram__bytes_read.sum + dram__bytes_write.sum
-TRAFFIC[("helmholtz3d_n256", 2, "core@l2")] = 6.00e9 + 0.64549e9
+TRAFFIC[("helmholtz3d_n256", 2, "core@l2")] = 6.00e9 + 0.21187e9
 # every per-mode register pass of fourier6d_n16 reads and writes the whole tensor once
 TRAFFIC.update({("fourier6d_n16", 1, f"sep_reg@l{k}"): 1.073863e9 + 1.025651e9 for k in range(6)})
 

@@ -218,6 +218,8 @@ tb_status tb_free(tb_handle h) {
     if (h->ws.buf[1]) cudaFree(h->ws.buf[1]);
     if (h->ws.mbuf[0]) cudaFree(h->ws.mbuf[0]);
     if (h->ws.mbuf[1]) cudaFree(h->ws.mbuf[1]);
+    if (h->ws.cout[0]) cudaFree(h->ws.cout[0]);
+    if (h->ws.cout[1]) cudaFree(h->ws.cout[1]);
     if (h->ws.host_in) cudaFree(h->ws.host_in);
     if (h->ws.host_out) cudaFree(h->ws.host_out);
     for (int b = 0; b < 2; ++b) {
@@ -1115,7 +1117,8 @@ extern "C" tb_status tb_query(tb_handle h, tb_info *info) {
     info->core_entries = h->core_entries;
     info->factor_entries = fe;
     info->level_entries_max = h->level_max;
-    info->device_bytes = h->device_bytes + (int64_t)h->ws.bytes * 2 + (int64_t)(h->ws.mbytes[0] + h->ws.mbytes[1]);
+    info->device_bytes = h->device_bytes + (int64_t)h->ws.bytes * 2 + (int64_t)(h->ws.mbytes[0] + h->ws.mbytes[1]) +
+                         (int64_t)(h->ws.cout_bytes[0] + h->ws.cout_bytes[1]);
     info->build_seconds = h->build_seconds;
     if (h->separable) {
         int64_t ms = h->P, mt = h->P;
@@ -1746,7 +1749,8 @@ template <>
 const cx<float> *coreptr<float>(const tb_plan *h) { return h->core32; }
 
 // Split-BF16 tensor-core core contraction (complex64 tiles), 16 RHS per launch.
-tb_status core_pass_tc(const tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st) {
+tb_status core_pass_tc(const tb_plan *h, bool adjoint, const void *in, void *out, int64_t nv, cudaStream_t st,
+                       bool zero_pad = true) {
     const int d = h->d, Lc = h->Lc;
     const int dir = adjoint ? 1 : 0;
     const TileBuf<float> tin = tilebuf<float>(h, adjoint ? 1 : 0, Lc, (void *)in);
@@ -1769,6 +1773,7 @@ tb_status core_pass_tc(const tb_plan *h, bool adjoint, const void *in, void *out
         a.out_R[k] = tout.R[k];
     }
     a.nv = (int)nv;
+    a.zero_pad = zero_pad ? 1 : 0;
     a.err = h->d_err;
     for (int64_t v0 = 0; v0 < nv; v0 += 16) {
         a.v0 = (int)v0;
@@ -2175,6 +2180,7 @@ tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t
                      [&] { return level_pass<R>(h, p, adjoint, side, l, i, o, nv, st, T); });
     };
     int cur = 0;
+    const void *gin = nullptr;   // input of the next target-side pass
     TB_TRY(level(Pass::LeafIn, "leaf_in", first, 0, in, B[cur]));
     for (int l = 1; l <= Lc; ++l) {
         TB_TRY(level(Pass::Split, "split", first, l, B[cur], B[cur ^ 1]));
@@ -2199,17 +2205,63 @@ tb_status run_chain(tb_plan *h, bool adjoint, const void *in, void *out, int64_t
                 flops = 8.0 * (double)h->core_entries * nv;
             }
         }
-        const int core_kernels =
-            (precision == TB_PREC_C64_SPLITBF16 && !h->separable) ? (int)((nv + 15) / 16) : 1;
-        TB_TRY(timed("core", Lc, bytes, flops, core_kernels,
-                     [&] { return core_pass<R>(h, adjoint, B[cur], B[cur ^ 1], nv, st, precision); }));
-        cur ^= 1;
+        const bool tc_core = precision == TB_PREC_C64_SPLITBF16 && !h->separable;
+        const int core_kernels = tc_core ? (int)((nv + 15) / 16) : 1;
+        // the split-BF16 core writes its own buffer, whose padded entries keep
+        // their zeros between applies (not with caller-provided buffers)
+        const int dir = adjoint ? 1 : 0;
+        void *cdst = (tc_core && !bufs && h->ws.cout[dir] && h->ws.cout_nv[dir] == nv) ? h->ws.cout[dir] : nullptr;
+        TB_TRY(timed("core", Lc, bytes, flops, core_kernels, [&] {
+            if (cdst) return core_pass_tc(h, adjoint, B[cur], cdst, nv, st, false);
+            return core_pass<R>(h, adjoint, B[cur], B[cur ^ 1], nv, st, precision);
+        }));
+        if (!cdst) {
+            cur ^= 1;
+            gin = B[cur];
+        } else {
+            gin = cdst;   // B[cur], the core's input, is free again
+        }
     }
     for (int l = Lc; l >= 1; --l) {
-        TB_TRY(level(Pass::Gather, "gather", second, l, B[cur], B[cur ^ 1]));
+        TB_TRY(level(Pass::Gather, "gather", second, l, gin, B[cur ^ 1]));
         cur ^= 1;
+        gin = B[cur];
     }
-    TB_TRY(level(Pass::LeafOut, "leaf_out", second, 0, B[cur], out));
+    TB_TRY(level(Pass::LeafOut, "leaf_out", second, 0, gin, out));
+    return TB_OK;
+}
+
+// The split-BF16 core's output buffers (tb::Workspace::cout) for nv RHS: on
+// handles that apply split BF16, one per direction, holding zeros in every
+// padded entry.  They are (re)allocated when too small and cleared when nv
+// changes (the padded positions depend on nv); both take a device-wide
+// synchronisation, outside any stream capture.
+tb_status ensure_core_out(tb_plan *h, int64_t nv) {
+    if (h->separable || !(h->precisions & (1u << TB_PREC_C64_SPLITBF16))) return TB_OK;
+    for (int dir = 0; dir < 2; ++dir) {
+        const TileBuf<float> t = tilebuf<float>(h, dir == 0 ? 1 : 0, h->Lc, nullptr);
+        const int64_t entries = h->P * (int64_t)t.tsize;
+        if ((uint64_t)nv > (uint64_t)(SIZE_MAX / sizeof(c64)) / (uint64_t)std::max<int64_t>(entries, 1))
+            return fail(TB_ENOMEM, "core output size for nv = " + std::to_string(nv) + " overflows");
+        const size_t need = (size_t)entries * (size_t)nv * sizeof(c64);
+        if (need > h->ws.cout_bytes[dir]) {
+            TB_CK(cudaDeviceSynchronize());
+            for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+            h->graphs.clear();
+            if (h->ws.cout[dir]) cudaFree(h->ws.cout[dir]);
+            h->ws.cout[dir] = nullptr;
+            h->ws.cout_bytes[dir] = 0;
+            h->ws.cout_nv[dir] = 0;
+            TB_CK(cudaMalloc(&h->ws.cout[dir], need));
+            h->ws.cout_bytes[dir] = need;
+        }
+        if (h->ws.cout_nv[dir] != nv) {
+            TB_CK(cudaDeviceSynchronize());
+            TB_CK(cudaMemset(h->ws.cout[dir], 0, need));
+            TB_CK(cudaDeviceSynchronize());
+            h->ws.cout_nv[dir] = nv;
+        }
+    }
     return TB_OK;
 }
 
@@ -2220,6 +2272,7 @@ tb_status ensure_workspace(tb_plan *h, int64_t nv) {
     const size_t need = (size_t)h->level_max * (size_t)nv * sizeof(c128);
     const size_t mneed[2] = {(size_t)h->mode_max[0] * (size_t)nv * sizeof(c128),
                              (size_t)h->mode_max[1] * (size_t)nv * sizeof(c128)};
+    TB_TRY(ensure_core_out(h, nv));
     if (need <= h->ws.bytes && mneed[0] <= h->ws.mbytes[0] && mneed[1] <= h->ws.mbytes[1]) return TB_OK;
     TB_CK(cudaDeviceSynchronize());
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);

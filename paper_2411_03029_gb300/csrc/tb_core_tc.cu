@@ -383,12 +383,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
         // compact entries (index < r_k in every mode) are written by the
         // epilogue, the rest must read as zero.  This role walks the block's
         // items with tile 0 (one per pair) and clears the others, one 16-RHS
-        // run per entry, independently of the MMA pipeline.
+        // run per entry, independently of the MMA pipeline.  Skipped when the
+        // output buffer keeps zeros there from one apply to the next.
         const int pt = tid - PAD_WARP0 * 32;
         int inner = 1;
         for (int k = 1; k < d; ++k) inner *= a.out_R[k];
         const bool vec = (a.nv & 1) == 0;
-        for (int64_t item = blockIdx.x; item < a.nitems && !*abort; item += gridDim.x) {
+        for (int64_t item = blockIdx.x; a.zero_pad && item < a.nitems && !*abort; item += gridDim.x) {
             const CoreItem it = a.items[item];
             if (it.tile != 0) continue;
             const int *rout = it.rout;

@@ -289,6 +289,7 @@ struct CoreTcArgs {
     int in_R[MAXD], out_R[MAXD];
     int nv;         // RHS stride of the tiles
     int v0, nvc;    // RHS chunk [v0, v0 + nvc) handled by this launch, nvc <= 16
+    int zero_pad;   // 1: write zeros to the padded output entries; 0: they already hold zeros
     int *err;
 };
 

@@ -33,6 +33,13 @@ struct Workspace {
     size_t bytes = 0;          // per buffer
     void *mbuf[2] = {nullptr, nullptr};   // mode intermediates of the level passes
     size_t mbytes[2] = {0, 0};
+    // output of the split-BF16 core per direction ([0] forward: target side,
+    // [1] adjoint: source side), laid out for cout_nv RHS; its padded entries
+    // hold zeros (set at allocation and when nv changes; the core writes only
+    // the compact entries)
+    void *cout[2] = {nullptr, nullptr};
+    size_t cout_bytes[2] = {0, 0};
+    int64_t cout_nv[2] = {0, 0};
     void *host_in = nullptr;   // device staging for tb_apply_host
     void *host_out = nullptr;
     size_t host_bytes = 0;

@@ -236,6 +236,28 @@ def test_splitbf16_core_multilevel_and_deterministic():
     assert np.array_equal(ubf, again)
 
 
+def test_splitbf16_core_output_keeps_zero_padding_across_rhs_counts():
+    # the split-BF16 core writes a buffer of its own whose padded entries keep the
+    # zeros of its allocation (the core writes only compact entries); a change of
+    # nv re-lays that buffer out and must clear it again.  RHS columns are
+    # independent, so 5 RHS give exactly the first 5 columns of 16.
+    w = W.small("helmholtz3d_n256", 32, nv=16, L=2, params=(2 * np.pi * 8,))
+    op = tb.from_workload(w, precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C64_SPLITBF16),
+                          level_schedule=tb.LEVEL_PER_MODE)
+    f16 = W.rhs(w).to(torch.complex64).cuda()
+    f5 = f16[..., :5].contiguous()
+    for adj in (False, True):
+        run = (lambda x, p: op.apply_adjoint(x, p)) if adj else (lambda x, p: op.apply(x, p))
+        a = run(f16, tb.PREC_C64_SPLITBF16).clone()
+        b = run(f5, tb.PREC_C64_SPLITBF16).clone()
+        c = run(f16, tb.PREC_C64_SPLITBF16).clone()
+        assert torch.equal(b, a[..., :5]), adj
+        assert torch.equal(a, c), adj
+        ref = run(f16, tb.PREC_C64).cpu().to(torch.complex128).numpy()
+        assert rel(a.cpu().to(torch.complex128).numpy(), ref) < 1e-4
+    op.close()
+
+
 # ------------------------------------------- register-resident separable chains
 @pytest.mark.parametrize("d,n,nv,precs", [(3, 16, 3, (tb.PREC_C64,)), (4, 8, 2, (tb.PREC_C64, tb.PREC_C128)),
                                           (2, 32, 4, (tb.PREC_C64,)), (6, 4, 5, (tb.PREC_C64, tb.PREC_C128))])
