@@ -1166,6 +1166,7 @@ FacRef<R> facref(const tb_plan *h, int side, int l) {
     std::memset(&f, 0, sizeof(f));
     for (int k = 0; k < h->d; ++k) {
         f.A[k] = facptr<R>(S, k);
+        f.rank[k] = S.rank[k];
         f.rows[k] = S.R[k];
         f.cols[k] = S.cin[k];
     }
@@ -1231,7 +1232,7 @@ int mode_ob_rule(int o) {
 template <class R>
 tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out, int64_t nv,
                      cudaStream_t st, void *const *T, int only_k = -1, int ob_set = 0, int waves_set = 0,
-                     int64_t f0 = 0, int64_t f1 = -1) {
+                     int64_t f0 = 0, int64_t f1 = -1, int rank_set = -1) {
     const int d = h->d, Lc = h->Lc;
     const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
     ModeArgs<R> a;
@@ -1354,7 +1355,10 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
         if (a.smem > g_smem_optin)
             return fail(TB_EUNSUPPORTED, "factor blocks of " + std::to_string(a.smem) +
                                              " bytes exceed shared memory");
-        TB_CK(launch_mode<R>(ink, outk, ob, a, st));
+        // rank-bounded products: the tuner's choice, else on for Split / Gather
+        // (their blocks' ranks spread below the padded length), off for the leaves
+        const int rk = rank_set >= 0 ? rank_set : (tune[k].rank >= 0 ? tune[k].rank : (leaf ? 0 : 1));
+        TB_CK(launch_mode<R>(ink, outk, ob, rk, a, st));
     }
     return TB_OK;
 }
@@ -2460,20 +2464,23 @@ tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, cons
                         tb::ModeTune best;
                         float tbest = 3.0e38f;
                         for (int i = 0; i < nob && status == TB_OK; ++i)
-                            for (int w : waves) {
-                                float t = 0.f;
-                                status = time_it(
-                                    [&] {
-                                        return level_pass<R>(h, p, false, side, l, in, out, nv, st, T, k, obs[i], w);
-                                    },
-                                    t);
-                                if (status != TB_OK) break;
-                                if (t < tbest) {
-                                    tbest = t;
-                                    best.ob = obs[i];
-                                    best.waves = w;
+                            for (int w : waves)
+                                for (int rk = 0; rk < 2 && status == TB_OK; ++rk) {
+                                    float t = 0.f;
+                                    status = time_it(
+                                        [&] {
+                                            return level_pass<R>(h, p, false, side, l, in, out, nv, st, T, k, obs[i],
+                                                                 w, 0, -1, rk);
+                                        },
+                                        t);
+                                    if (status != TB_OK) break;
+                                    if (t < tbest) {
+                                        tbest = t;
+                                        best.ob = obs[i];
+                                        best.waves = w;
+                                        best.rank = rk;
+                                    }
                                 }
-                            }
                         h->tune[ri][side][(int)p][l][k] = best;
                     }
                 }

@@ -83,6 +83,7 @@ struct TileBuf {
 template <class R>
 struct FacRef {
     const cx<R> *A[MAXD];
+    const int *rank[MAXD];   // rank of each block (its rows past the rank are zero); may be null
     int rows[MAXD], cols[MAXD];
     int l, lgseg;
     int64_t nM;
@@ -96,17 +97,18 @@ TB_DEV int64_t tile_index(const TileBuf<R> &b, int64_t F, int64_t M, int64_t sfl
     return (blk << (b.lgseg * d)) + sflat;
 }
 
+// Index of the factor block of mode k for (F, M, segment sig) at the factor's level.
+template <class R>
+TB_DEV int64_t fac_index(const FacRef<R> &f, int k, int64_t F, int64_t M, int sig, int d, int Lc) {
+    if (!f.separable) return ((F * f.nM + M) << f.lgseg) + sig;
+    const int64_t Fk = (F >> (Lc * (d - 1 - k))) & ((1 << Lc) - 1);
+    const int64_t Mk = (M >> (f.l * (d - 1 - k))) & ((1 << f.l) - 1);
+    return (((Fk << f.l) + Mk) << f.lgseg) + sig;
+}
 // Factor block of mode k for (F, M, segment sig) at the factor's level.
 template <class R>
 TB_DEV const cx<R> *fac_block(const FacRef<R> &f, int k, int64_t F, int64_t M, int sig, int d, int Lc) {
-    int64_t j;
-    if (!f.separable) j = ((F * f.nM + M) << f.lgseg) + sig;
-    else {
-        const int64_t Fk = (F >> (Lc * (d - 1 - k))) & ((1 << Lc) - 1);
-        const int64_t Mk = (M >> (f.l * (d - 1 - k))) & ((1 << f.l) - 1);
-        j = (((Fk << f.l) + Mk) << f.lgseg) + sig;
-    }
-    return f.A[k] + j * (int64_t)f.rows[k] * f.cols[k];
+    return f.A[k] + fac_index<R>(f, k, F, M, sig, d, Lc) * (int64_t)f.rows[k] * f.cols[k];
 }
 
 template <class R>
@@ -148,7 +150,7 @@ struct ModeArgs {
 };
 
 template <class R>
-cudaError_t launch_mode(int in_kind, int out_kind, int ob, const ModeArgs<R> &a, cudaStream_t st);
+cudaError_t launch_mode(int in_kind, int out_kind, int ob, int rank, const ModeArgs<R> &a, cudaStream_t st);
 int mode_cols_per_block();
 
 // A whole level pass (all d mode products) in one persistent launch

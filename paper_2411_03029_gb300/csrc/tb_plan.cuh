@@ -81,6 +81,7 @@ struct LevelTune {
 struct ModeTune {
     int ob = 0;      // output rows per register tile
     int waves = 0;   // thread blocks per SM the grid is sized for
+    int rank = -1;   // rank-bounded products (1) or not (0); -1: the built-in rule
 };
 
 struct GraphEntry {
