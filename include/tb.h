@@ -339,8 +339,11 @@ tb_status tb_shard_plan(int64_t nmid, int nranks, int64_t *begin, int64_t *end);
  * `precision`, on the handle's own factors and workspaces (the paper fixes no
  * launch layout; this is the library's own schedule search):
  *  - non-separable handles: for every level pass, side and mode, the output
- *    rows per register tile (even values up to 16) and the number of thread
- *    blocks per unit;
+ *    rows per register tile (even values up to 24), the number of thread
+ *    blocks per unit, the rank bounds (on or off) and the threads per block
+ *    (the fewest covering a unit's columns, or 128); per pass, the fused,
+ *    tensor-core (split-BF16 applies) or per-mode form; for the one-RHS
+ *    forward core, stored or regenerated cores;
  *  - separable handles: per-mode passes with shared-memory fibers, with
  *    register-resident fibers (where the chain has the exact-rank form; see
  *    tb_options.sep_schedule) and multi-mode tile passes.

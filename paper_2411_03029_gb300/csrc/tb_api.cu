@@ -1218,6 +1218,18 @@ tb_status pick_chunk(int d, const int *m, const int *o, int64_t nv, int64_t &nvc
 // (even, up to 16, and 18, 20, 24), and the built-in rule: the fewest chunks
 // of at most 24 rows, split evenly.
 bool mode_ob_valid(int ob) { return ob >= 2 && !(ob & 1) && (ob <= 20 || ob == 24); }
+
+// Threads per block of a mode launch: `want` if valid (32, 64 or 128, and at
+// least `minbt`), else the fewest that cover `cols` columns (at least minbt).
+int mode_bt(int want, int64_t cols, int minbt) {
+    const int lo = minbt <= 32 ? 32 : 64;
+    if ((want == 32 || want == 64 || want == 128) && want >= lo) return want;
+    const int64_t per = (int64_t)mode_cols_per_thread();
+    int bt = 128;
+    if (cols <= 32 * per) bt = 32;
+    else if (cols <= 64 * per) bt = 64;
+    return bt < lo ? lo : bt;
+}
 int mode_ob_rule(int o) {
     const int nch = (o + 23) / 24;
     int ob = (o + nch - 1) / nch;
@@ -1232,7 +1244,7 @@ int mode_ob_rule(int o) {
 template <class R>
 tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out, int64_t nv,
                      cudaStream_t st, void *const *T, int only_k = -1, int ob_set = 0, int waves_set = 0,
-                     int64_t f0 = 0, int64_t f1 = -1, int rank_set = -1) {
+                     int64_t f0 = 0, int64_t f1 = -1, int rank_set = -1, int bt_set = 0, int *bt_used = nullptr) {
     const int d = h->d, Lc = h->Lc;
     const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
     ModeArgs<R> a;
@@ -1339,7 +1351,12 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
         a.nblk = (!leaf && group) ? (h->P >> d) : h->P;
         if (a.cols >= ((int64_t)1 << 31) || usz_in >= ((int64_t)1 << 31) || usz_out >= ((int64_t)1 << 31))
             return fail(TB_EUNSUPPORTED, "a level tile with its RHS exceeds 2^31 entries (reduce nv)");
-        const int cpb = mode_cols_per_block();
+        // threads per block: the tuner's choice, else the fewest (32, 64 or 128)
+        // that give one column to each of a unit's columns; a group launch sets
+        // up its 2^d children with one thread each
+        a.bt = mode_bt(bt_set ? bt_set : tune[k].bt, a.cols, group ? (1 << d) : 1);
+        if (bt_used) *bt_used = a.bt;
+        const int cpb = a.bt * mode_cols_per_thread();
         a.ncb = (a.cols + cpb - 1) / cpb;
         // enough blocks for a few waves of four resident blocks per SM
         const int waves = waves_set ? waves_set : (tune[k].waves > 0 ? tune[k].waves : TB_MODE_WAVES);
@@ -2461,26 +2478,32 @@ tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, cons
                             for (int i = 0; i < nob; ++i) dup = dup || obs[i] == ob;
                             if (!dup) obs[nob++] = ob;
                         }
+                        // threads per block: the built-in (fewest covering a unit) and 128
+                        const int bts[2] = {0, 128};
                         tb::ModeTune best;
                         float tbest = 3.0e38f;
                         for (int i = 0; i < nob && status == TB_OK; ++i)
                             for (int w : waves)
-                                for (int rk = 0; rk < 2 && status == TB_OK; ++rk) {
-                                    float t = 0.f;
-                                    status = time_it(
-                                        [&] {
-                                            return level_pass<R>(h, p, false, side, l, in, out, nv, st, T, k, obs[i],
-                                                                 w, 0, -1, rk);
-                                        },
-                                        t);
-                                    if (status != TB_OK) break;
-                                    if (t < tbest) {
-                                        tbest = t;
-                                        best.ob = obs[i];
-                                        best.waves = w;
-                                        best.rank = rk;
+                                for (int rk = 0; rk < 2 && status == TB_OK; ++rk)
+                                    for (int bi = 0, bt0 = 0; bi < 2 && status == TB_OK; ++bi) {
+                                        if (bi == 1 && bt0 == 128) continue;   // the same launch as bi = 0
+                                        float t = 0.f;
+                                        status = time_it(
+                                            [&] {
+                                                return level_pass<R>(h, p, false, side, l, in, out, nv, st, T, k,
+                                                                     obs[i], w, 0, -1, rk, bts[bi],
+                                                                     bi == 0 ? &bt0 : nullptr);
+                                            },
+                                            t);
+                                        if (status != TB_OK) break;
+                                        if (t < tbest) {
+                                            tbest = t;
+                                            best.ob = obs[i];
+                                            best.waves = w;
+                                            best.rank = rk;
+                                            best.bt = bts[bi];
+                                        }
                                     }
-                                }
                         h->tune[ri][side][(int)p][l][k] = best;
                     }
                 }

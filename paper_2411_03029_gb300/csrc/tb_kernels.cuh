@@ -132,6 +132,7 @@ struct ModeArgs {
     int64_t pre, post, cols;   // columns of one unit
     int64_t nblk, ncb;         // units (or groups) of the launch, column chunks per unit
     int64_t gsplit;            // thread blocks per unit; each walks every gsplit-th chunk
+    int bt;                    // threads per block (32, 64 or 128; at least 2^d for a group launch)
     int64_t nv, nF;
     int lvl, lgs;              // factor level and segment bits per mode of the pass's tiles
     int in_tile, out_tile;     // MK_UNIT input / output is the level tile instead of a unit buffer
@@ -151,7 +152,7 @@ struct ModeArgs {
 
 template <class R>
 cudaError_t launch_mode(int in_kind, int out_kind, int ob, int rank, const ModeArgs<R> &a, cudaStream_t st);
-int mode_cols_per_block();
+int mode_cols_per_thread();
 
 // A whole level pass (all d mode products) in one persistent launch
 // (k_level in tb_level.cu), complex64.  Work item = (unit or group, chunk of

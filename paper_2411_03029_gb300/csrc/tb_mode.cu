@@ -15,7 +15,7 @@ cudaError_t launch_mode(int in_kind, int out_kind, int ob, int rank, const ModeA
                 : launch_mode_rk<R, false>(in_kind, out_kind, ob, a, st);
 }
 
-int mode_cols_per_block() { return MODE_THREADS * MODE_NC; }
+int mode_cols_per_thread() { return MODE_NC; }
 
 template cudaError_t launch_mode<float>(int, int, int, int, const ModeArgs<float> &, cudaStream_t);
 template cudaError_t launch_mode<double>(int, int, int, int, const ModeArgs<double> &, cudaStream_t);

@@ -176,7 +176,8 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
     }
 
     int my_rk = 0;   // rank of child tid's factor block (its load overlaps the factor staging)
-    if (tid < 64) {
+    const int bt = a.bt, pt = bt < 64 ? bt : 64;   // threads per block, of them setting up
+    if (tid < pt) {
         // ---- the unit (or group) of this block
         const int Lc = a.Lc, lgs = a.lgs, lvl = a.lvl;
         int64_t g = blk;
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
         if (USER) {
             for (int i = 0; i < d; ++i) {
                 const int64_t Fi = (F >> (Lc * (d - 1 - i))) & ((1 << Lc) - 1);
-                for (int b = j; b < a.cb[i]; b += 64)
+                for (int b = j; b < a.cb[i]; b += pt)
                     gt[goff[i] + b] = a.perm[i][Fi * a.nmid[i] + (int64_t)sig[i] * a.cb[i] + b];
             }
         }
@@ -244,13 +245,13 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
     const bool trans = a.trans != 0;
     const int post = (int)a.post, nv = (int)a.nv, cols = (int)a.cols;
     for (unsigned cblk = cfirst; cblk < (unsigned)a.ncb; cblk += (unsigned)a.gsplit) {
-    const int col0 = (int)cblk * (MODE_THREADS * NC) + tid;
+    const int col0 = (int)cblk * (bt * NC) + tid;
     if (col0 >= cols) break;
     bool valid[NC];
     int pcol[NC], qcol[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        int cc = col0 + j * MODE_THREADS;
+        int cc = col0 + j * bt;
         valid[j] = cc < cols;
         if (!valid[j]) cc = cols - 1;   // computes a duplicate, stores nothing
         pcol[j] = cc / post;
@@ -484,7 +485,8 @@ cudaError_t launch_mode_ob(int ob, const ModeArgs<R> &a, cudaStream_t st) {
     const int64_t blocks = a.nblk * a.gsplit;
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
-    fn<<<(unsigned)blocks, MODE_THREADS, a.smem, st>>>(a);
+    if (a.bt != 32 && a.bt != 64 && a.bt != MODE_THREADS) return cudaErrorInvalidValue;
+    fn<<<(unsigned)blocks, (unsigned)a.bt, a.smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -82,6 +82,7 @@ struct ModeTune {
     int ob = 0;      // output rows per register tile
     int waves = 0;   // thread blocks per SM the grid is sized for
     int rank = -1;   // rank-bounded products (1) or not (0); -1: the built-in rule
+    int bt = 0;      // threads per block (32, 64, 128); 0: the built-in rule
 };
 
 struct GraphEntry {
