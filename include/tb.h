@@ -139,6 +139,12 @@ typedef struct {
                                   grids, where |x - y|^2 and x.xi are exact integers in
                                   grid units; else 1).  The cores stay stored: the adjoint
                                   and several-RHS contractions read them */
+    int mode_slices;       /* complex64 per-mode level launches: groups of threads that share
+                              each output column (each takes every n-th child / row chunk of
+                              it), for units with few columns; 0 = built-in rule (1;
+                              tb_autotune may pick 2 or 4 per launch), 1, 2 or 4 = that many
+                              for every launch (at most 128 threads per block; complex128
+                              always uses 1).  Results do not depend on it. */
 } tb_options;
 
 typedef struct tb_plan *tb_handle;

@@ -59,7 +59,7 @@ class _Options(ctypes.Structure):
                 ("rank_max", ctypes.c_int), ("precisions", ctypes.c_uint), ("separable", ctypes.c_int),
                 ("use_graphs", ctypes.c_int), ("device", ctypes.c_int), ("seed", ctypes.c_uint64),
                 ("autotune", ctypes.c_int), ("sep_schedule", ctypes.c_int), ("level_schedule", ctypes.c_int),
-                ("core_mode", ctypes.c_int)]
+                ("core_mode", ctypes.c_int), ("mode_slices", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -155,7 +155,7 @@ class TBOperator:
                  order: int = ORDER_AUTO, precisions: int = 0, separable: int = -1,
                  use_graphs: bool = False, proxy_rows: int = 1024, rank_max: int = 32,
                  seed: int = 0x5eed, precision: int = PREC_C64, autotune: bool = False,
-                 sep_schedule: int = 0, level_schedule: int = 0, core_mode: int = 0):
+                 sep_schedule: int = 0, level_schedule: int = 0, core_mode: int = 0, mode_slices: int = 0):
         L_ = lib()
         n = [int(v) for v in (n if np.iterable(n) else [n] * d)]
         self.d, self.n, self.kind = d, n, kind
@@ -175,6 +175,7 @@ class TBOperator:
         opt.sep_schedule = int(sep_schedule)
         opt.level_schedule = int(level_schedule)
         opt.core_mode = int(core_mode)
+        opt.mode_slices = int(mode_slices)
         try:
             opt.device = _torch().cuda.current_device()
         except Exception:  # pragma: no cover

@@ -56,7 +56,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1))) as ex:
         results = list(ex.map(compile_one, sources()))
     if verbose or ptxas_v:
         for _, err in results:

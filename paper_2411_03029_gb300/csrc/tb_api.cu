@@ -203,6 +203,7 @@ tb_status tb_options_default(tb_options *o) {
     o->sep_schedule = 0;
     o->level_schedule = 0;
     o->core_mode = 0;
+    o->mode_slices = 0;
     return TB_OK;
 }
 
@@ -1035,6 +1036,8 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     if (opt.sep_schedule < 0 || opt.sep_schedule > 6) return fail(TB_EINVAL, "sep_schedule must be in [0, 6]");
     if (opt.level_schedule < 0 || opt.level_schedule > 3) return fail(TB_EINVAL, "level_schedule must be in [0, 3]");
     if (opt.core_mode < 0 || opt.core_mode > 2) return fail(TB_EINVAL, "core_mode must be in [0, 2]");
+    if (opt.mode_slices != 0 && opt.mode_slices != 1 && opt.mode_slices != 2 && opt.mode_slices != 4)
+        return fail(TB_EINVAL, "mode_slices must be 0, 1, 2 or 4");
     int dev = opt.device;
     if (dev < 0) {
         if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return fail(TB_ECUDA, "no CUDA device"); }
@@ -1065,6 +1068,7 @@ extern "C" tb_status tb_build_ex(const tb_kernel *kernel, int d, const int64_t *
     h->sep_choice = opt.sep_schedule;
     h->level_choice = opt.level_schedule;
     h->core_mode = opt.core_mode;
+    h->mode_slices = opt.mode_slices;
     h->proxy_rows = opt.proxy_rows;
     h->rank_max = opt.rank_max;
     h->seed = opt.seed;
@@ -1244,7 +1248,8 @@ int mode_ob_rule(int o) {
 template <class R>
 tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, const void *in, void *out, int64_t nv,
                      cudaStream_t st, void *const *T, int only_k = -1, int ob_set = 0, int waves_set = 0,
-                     int64_t f0 = 0, int64_t f1 = -1, int rank_set = -1, int bt_set = 0, int *bt_used = nullptr) {
+                     int64_t f0 = 0, int64_t f1 = -1, int rank_set = -1, int bt_set = 0, int *bt_used = nullptr,
+                     int sub_set = 0) {
     const int d = h->d, Lc = h->Lc;
     const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
     ModeArgs<R> a;
@@ -1351,12 +1356,18 @@ tb_status level_pass(const tb_plan *h, Pass pass, bool conj, int side, int l, co
         a.nblk = (!leaf && group) ? (h->P >> d) : h->P;
         if (a.cols >= ((int64_t)1 << 31) || usz_in >= ((int64_t)1 << 31) || usz_out >= ((int64_t)1 << 31))
             return fail(TB_EUNSUPPORTED, "a level tile with its RHS exceeds 2^31 entries (reduce nv)");
-        // threads per block: the tuner's choice, else the fewest (32, 64 or 128)
-        // that give one column to each of a unit's columns; a group launch sets
-        // up its 2^d children with one thread each
-        a.bt = mode_bt(bt_set ? bt_set : tune[k].bt, a.cols, group ? (1 << d) : 1);
-        if (bt_used) *bt_used = a.bt;
-        const int cpb = a.bt * mode_cols_per_thread();
+        // threads per column slice: the tuner's choice, else the fewest (32, 64
+        // or 128) that give one thread to each of a unit's columns; a group
+        // launch sets up its 2^d children with one thread each.  sub slices
+        // (1, 2 or 4; at most 128 threads) share each column's work.
+        const int cw = mode_bt(bt_set ? bt_set : tune[k].bt, a.cols, group ? (1 << d) : 1);
+        if (bt_used) *bt_used = cw;
+        int sub = sub_set ? sub_set : (h->mode_slices ? h->mode_slices : (tune[k].sub > 0 ? tune[k].sub : 1));
+        if ((sub != 1 && sub != 2 && sub != 4) || sizeof(R) != 4) sub = 1;   // slices: complex64 only
+        while (sub > 1 && sub * cw > 128) sub >>= 1;
+        a.sub = sub;
+        a.bt = sub * cw;
+        const int cpb = cw * mode_cols_per_thread();
         a.ncb = (a.cols + cpb - 1) / cpb;
         // enough blocks for a few waves of four resident blocks per SM
         const int waves = waves_set ? waves_set : (tune[k].waves > 0 ? tune[k].waves : TB_MODE_WAVES);
@@ -2478,32 +2489,37 @@ tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, cons
                             for (int i = 0; i < nob; ++i) dup = dup || obs[i] == ob;
                             if (!dup) obs[nob++] = ob;
                         }
-                        // threads per block: the built-in (fewest covering a unit) and 128
+                        // threads per column slice: the built-in (fewest covering a unit)
+                        // and 128; slices per column: 1, 2, 4 (up to 128 threads)
                         const int bts[2] = {0, 128};
                         tb::ModeTune best;
                         float tbest = 3.0e38f;
                         for (int i = 0; i < nob && status == TB_OK; ++i)
                             for (int w : waves)
                                 for (int rk = 0; rk < 2 && status == TB_OK; ++rk)
-                                    for (int bi = 0, bt0 = 0; bi < 2 && status == TB_OK; ++bi) {
-                                        if (bi == 1 && bt0 == 128) continue;   // the same launch as bi = 0
-                                        float t = 0.f;
-                                        status = time_it(
-                                            [&] {
-                                                return level_pass<R>(h, p, false, side, l, in, out, nv, st, T, k,
-                                                                     obs[i], w, 0, -1, rk, bts[bi],
-                                                                     bi == 0 ? &bt0 : nullptr);
-                                            },
-                                            t);
-                                        if (status != TB_OK) break;
-                                        if (t < tbest) {
-                                            tbest = t;
-                                            best.ob = obs[i];
-                                            best.waves = w;
-                                            best.rank = rk;
-                                            best.bt = bts[bi];
+                                    for (int bi = 0, bt0 = 0; bi < 2 && status == TB_OK; ++bi)
+                                        for (int sb = 1; sb <= 4 && status == TB_OK; sb *= 2) {
+                                            if (bi == 1 && bt0 == 128) break;   // the same launches as bi = 0
+                                            const int cw = bi == 0 ? bt0 : bts[bi];
+                                            if (sb > 1 && (sb * cw > 128 || ri)) break;
+                                            float t = 0.f;
+                                            status = time_it(
+                                                [&] {
+                                                    return level_pass<R>(h, p, false, side, l, in, out, nv, st, T, k,
+                                                                         obs[i], w, 0, -1, rk, bts[bi],
+                                                                         (bi == 0 && sb == 1) ? &bt0 : nullptr, sb);
+                                                },
+                                                t);
+                                            if (status != TB_OK) break;
+                                            if (t < tbest) {
+                                                tbest = t;
+                                                best.ob = obs[i];
+                                                best.waves = w;
+                                                best.rank = rk;
+                                                best.bt = bts[bi];
+                                                best.sub = sb;
+                                            }
                                         }
-                                    }
                         h->tune[ri][side][(int)p][l][k] = best;
                     }
                 }

@@ -133,6 +133,7 @@ struct ModeArgs {
     int64_t nblk, ncb;         // units (or groups) of the launch, column chunks per unit
     int64_t gsplit;            // thread blocks per unit; each walks every gsplit-th chunk
     int bt;                    // threads per block (32, 64 or 128; at least 2^d for a group launch)
+    int sub;                   // slices of bt / sub threads (a multiple of 32) sharing each column slot
     int64_t nv, nF;
     int lvl, lgs;              // factor level and segment bits per mode of the pass's tiles
     int in_tile, out_tile;     // MK_UNIT input / output is the level tile instead of a unit buffer

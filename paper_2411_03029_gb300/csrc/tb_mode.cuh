@@ -124,10 +124,10 @@ TB_DEV void mode_rows(cx<R> (&acc)[NC][OB], const cx<R> *__restrict__ At, int ld
     }
 }
 
-// Stage an r x c factor block as dst[b * lda + a] = op(A)[a][b] (op = A or
+// Stage one r x c factor block as dst[b * lda + a] = op(A)[a][b] (op = A or
 // A^T, optionally conjugated), zero for a >= o.
 template <class R>
-TB_DEV void stage_fac(cx<R> *dst, const cx<R> *__restrict__ src, int r, int c, bool trans, bool cj, int lda) {
+TB_DEV void stage_fac1(cx<R> *dst, const cx<R> *__restrict__ src, int r, int c, bool trans, bool cj, int lda) {
     const int o = trans ? c : r, m = trans ? r : c;
     for (int e = threadIdx.x; e < m * lda; e += blockDim.x) {
         const int b = e / lda, aa = e - b * lda;
@@ -140,7 +140,40 @@ TB_DEV void stage_fac(cx<R> *dst, const cx<R> *__restrict__ src, int r, int c, b
     }
 }
 
-template <class R, int IN, int OUT, int OB, bool RK>
+// Stage the r x c factor blocks src[j] of nb children (a group), child j as
+// dst[j * fsz + b * lda + a] = op(A_j)[a][b] (op = A or A^T, optionally
+// conjugated; b < m = c or r), zero for a >= o and b >= m.  Each thread loads 8 entries
+// before it stores any, so a small block keeps several loads in flight.
+template <class R>
+TB_DEV void stage_fac(cx<R> *dst, const cx<R> *const *src, int nb, int fsz, int r, int c, bool trans, bool cj,
+                      int lda) {
+    constexpr int SB = 8;
+    const int o = trans ? c : r, m = trans ? r : c;
+    const int n = nb * fsz, st = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < n; e0 += SB * st) {
+        cx<R> v[SB];
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+            const int e = e0 + u * st;
+            v[u] = {R(0), R(0)};
+            if (e < n) {
+                const int j = e / fsz, rem = e - j * fsz;
+                const int b = rem / lda, aa = rem - b * lda;
+                if (aa < o && b < m) v[u] = trans ? src[j][b * c + aa] : src[j][aa * c + b];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < SB; ++u) {
+            const int e = e0 + u * st;
+            if (e < n) {
+                if (cj) v[u].y = -v[u].y;
+                dst[e] = v[u];
+            }
+        }
+    }
+}
+
+template <class R, int IN, int OUT, int OB, bool RK, bool SL>
 #ifndef TB_MODE_MINB
 #define TB_MODE_MINB 6   // complex64: resident blocks per SM the register allocation must allow
 #endif
@@ -235,23 +268,36 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
     }
     __syncthreads();
     if (s_skip) return;   // block-uniform
-    for (int j = 0; j < nchild; ++j)
-        stage_fac<R>(As + (int64_t)j * a.fsz, s_fac[j], a.fac.rows[k], a.fac.cols[k], a.trans != 0, a.conj != 0,
-                     a.lda);
+    // one entry per thread: the plain loop; more: batched loads (a group always)
+    if (!GROUP && a.fsz <= bt)
+        stage_fac1<R>(As, s_fac[0], a.fac.rows[k], a.fac.cols[k], a.trans != 0, a.conj != 0, a.lda);
+    else
+        stage_fac<R>(As, s_fac, nchild, a.fsz, a.fac.rows[k], a.fac.cols[k], a.trans != 0, a.conj != 0, a.lda);
     if (tid < nchild) s_rk[tid] = my_rk;
     __syncthreads();
 
     const int m = a.m, o = a.o, lda = a.lda;
     const bool trans = a.trans != 0;
     const int post = (int)a.post, nv = (int)a.nv, cols = (int)a.cols;
+    // S = a.sub warps-or-wider slices of the block share each column slot: slice
+    // `sub` takes every S-th (child, row chunk) item of its column
+    // SL: S = a.sub slices of cw = bt / S threads share each column slot
+    // (S = 2 or 4); slice `sub` takes every S-th (child, row chunk) item
+    const int S = SL ? a.sub : 1, cw = SL ? bt / S : bt;
+    const int sub = SL ? tid / cw : 0, tc = SL ? tid - sub * cw : tid;
+    // item (child c, row chunk a0 / OB) of a Split group belongs to slice
+    // (c * chunks + a0 / OB) mod S (recomputed from the arguments: no live registers)
+    auto mine = [&](int c, int a0) {
+        return !SL || (((c * (a.lda / OB) + a0 / OB) & (a.sub - 1)) == (int)(threadIdx.x / (a.bt / a.sub)));
+    };
     for (unsigned cblk = cfirst; cblk < (unsigned)a.ncb; cblk += (unsigned)a.gsplit) {
-    const int col0 = (int)cblk * (bt * NC) + tid;
+    const int col0 = (int)cblk * (cw * NC) + tc;
     if (col0 >= cols) break;
     bool valid[NC];
     int pcol[NC], qcol[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-        int cc = col0 + j * bt;
+        int cc = col0 + j * cw;
         valid[j] = cc < cols;
         if (!valid[j]) cc = cols - 1;   // computes a duplicate, stores nothing
         pcol[j] = cc / post;
@@ -387,6 +433,7 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
                 const cx<R> *At = As + (int64_t)c * a.fsz;
                 const int aend = (RK && !trans) ? s_rk[c] : lda;
                 for (int a0 = 0; a0 < lda; a0 += OB) {
+                    if (!mine(c, a0)) continue;
                     cx<R> acc[NC][OB];
                     zero(acc);
                     if constexpr (RK) {
@@ -427,6 +474,7 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
                 const int aend = (RK && !trans) ? s_rk[c] : lda;
                 const int mc = (RK && trans) ? min(m, s_rk[c]) : m;
                 for (int a0 = 0; a0 < lda; a0 += OB) {
+                    if (!mine(c, a0)) continue;
                     cx<R> acc[NC][OB];
                     zero(acc);
                     if (a0 < aend) mode_rows<R, OB, NC, RK>(acc, As + (int64_t)c * a.fsz, lda, a0, aend, mc, ld);
@@ -439,7 +487,7 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
         cx<R> *Y = s_out[0];
         const int aend = (RK && !trans) ? s_rk[0] : lda;
         const int mc = (RK && trans) ? min(m, s_rk[0]) : m;
-        for (int a0 = 0; a0 < lda; a0 += OB) {
+        for (int a0 = SL ? sub * OB : 0; a0 < lda; a0 += SL ? S * OB : OB) {
             cx<R> acc[NC][OB];
             zero(acc);
             if (a0 < aend) mode_rows<R, OB, NC, RK>(acc, As, lda, a0, aend, mc, ld);
@@ -447,7 +495,7 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
         }
     } else {
         cx<R> *Y = s_out[0];
-        for (int a0 = 0; a0 < lda; a0 += OB) {
+        for (int a0 = SL ? sub * OB : 0; a0 < lda; a0 += SL ? S * OB : OB) {
             cx<R> acc[NC][OB];
             zero(acc);
             for (int c = 0; c < nchild; ++c) {   // children in a fixed order (Gather)
@@ -463,21 +511,21 @@ __global__ void __launch_bounds__(MODE_THREADS, sizeof(R) == 4 ? (OB <= 16 ? TB_
     }   // column chunks
 }
 
-template <class R, int IN, int OUT, bool RK>
+template <class R, int IN, int OUT, bool RK, bool SL>
 cudaError_t launch_mode_ob(int ob, const ModeArgs<R> &a, cudaStream_t st) {
     void (*fn)(const ModeArgs<R>) = nullptr;
     switch (ob) {
-        case 2: fn = k_mode<R, IN, OUT, 2, RK>; break;
-        case 4: fn = k_mode<R, IN, OUT, 4, RK>; break;
-        case 6: fn = k_mode<R, IN, OUT, 6, RK>; break;
-        case 8: fn = k_mode<R, IN, OUT, 8, RK>; break;
-        case 10: fn = k_mode<R, IN, OUT, 10, RK>; break;
-        case 12: fn = k_mode<R, IN, OUT, 12, RK>; break;
-        case 14: fn = k_mode<R, IN, OUT, 14, RK>; break;
-        case 16: fn = k_mode<R, IN, OUT, 16, RK>; break;
-        case 18: fn = k_mode<R, IN, OUT, 18, RK>; break;
-        case 20: fn = k_mode<R, IN, OUT, 20, RK>; break;
-        case 24: fn = k_mode<R, IN, OUT, 24, RK>; break;
+        case 2: fn = k_mode<R, IN, OUT, 2, RK, SL>; break;
+        case 4: fn = k_mode<R, IN, OUT, 4, RK, SL>; break;
+        case 6: fn = k_mode<R, IN, OUT, 6, RK, SL>; break;
+        case 8: fn = k_mode<R, IN, OUT, 8, RK, SL>; break;
+        case 10: fn = k_mode<R, IN, OUT, 10, RK, SL>; break;
+        case 12: fn = k_mode<R, IN, OUT, 12, RK, SL>; break;
+        case 14: fn = k_mode<R, IN, OUT, 14, RK, SL>; break;
+        case 16: fn = k_mode<R, IN, OUT, 16, RK, SL>; break;
+        case 18: fn = k_mode<R, IN, OUT, 18, RK, SL>; break;
+        case 20: fn = k_mode<R, IN, OUT, 20, RK, SL>; break;
+        case 24: fn = k_mode<R, IN, OUT, 24, RK, SL>; break;
         default: return cudaErrorInvalidValue;
     }
     cudaError_t e = set_smem_once((const void *)fn, a.smem);
@@ -486,20 +534,25 @@ cudaError_t launch_mode_ob(int ob, const ModeArgs<R> &a, cudaStream_t st) {
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffff) return cudaErrorInvalidConfiguration;
     if (a.bt != 32 && a.bt != 64 && a.bt != MODE_THREADS) return cudaErrorInvalidValue;
+    if (a.sub < 1 || (!SL && a.sub != 1) || a.bt % a.sub || (a.bt / a.sub) % 32) return cudaErrorInvalidValue;
     fn<<<(unsigned)blocks, (unsigned)a.bt, a.smem, st>>>(a);
     return cudaGetLastError();
 }
 
 // The per-mode launch of kinds (in_kind, out_kind), output rows per register
-// chunk ob, rank bounds on (RK) or off; instantiated in tb_mode.cu (off) and
-// tb_mode_rank.cu (on), which compile in parallel.
-template <class R, bool RK>
+// chunk ob, rank bounds on (RK) or off, column slices (SL, a.sub > 1) or not;
+// instantiated in tb_mode.cu (neither), tb_mode_rank.cu (RK), and
+// tb_mode_slice.cu / tb_mode_slice_rank.cu (SL, complex64), which compile in
+// parallel.
+template <class R, bool RK, bool SL>
 cudaError_t launch_mode_rk(int in_kind, int out_kind, int ob, const ModeArgs<R> &a, cudaStream_t st) {
-    if (in_kind == MK_USER && out_kind == MK_UNIT) return launch_mode_ob<R, MK_USER, MK_UNIT, RK>(ob, a, st);
-    if (in_kind == MK_PARENTS && out_kind == MK_UNIT) return launch_mode_ob<R, MK_PARENTS, MK_UNIT, RK>(ob, a, st);
-    if (in_kind == MK_UNIT && out_kind == MK_UNIT) return launch_mode_ob<R, MK_UNIT, MK_UNIT, RK>(ob, a, st);
-    if (in_kind == MK_UNIT && out_kind == MK_PARENTS) return launch_mode_ob<R, MK_UNIT, MK_PARENTS, RK>(ob, a, st);
-    if (in_kind == MK_UNIT && out_kind == MK_USER) return launch_mode_ob<R, MK_UNIT, MK_USER, RK>(ob, a, st);
+    if (in_kind == MK_USER && out_kind == MK_UNIT) return launch_mode_ob<R, MK_USER, MK_UNIT, RK, SL>(ob, a, st);
+    if (in_kind == MK_PARENTS && out_kind == MK_UNIT)
+        return launch_mode_ob<R, MK_PARENTS, MK_UNIT, RK, SL>(ob, a, st);
+    if (in_kind == MK_UNIT && out_kind == MK_UNIT) return launch_mode_ob<R, MK_UNIT, MK_UNIT, RK, SL>(ob, a, st);
+    if (in_kind == MK_UNIT && out_kind == MK_PARENTS)
+        return launch_mode_ob<R, MK_UNIT, MK_PARENTS, RK, SL>(ob, a, st);
+    if (in_kind == MK_UNIT && out_kind == MK_USER) return launch_mode_ob<R, MK_UNIT, MK_USER, RK, SL>(ob, a, st);
     return cudaErrorInvalidValue;
 }
 

@@ -5,7 +5,7 @@
 
 namespace tb {
 
-template cudaError_t launch_mode_rk<float, true>(int, int, int, const ModeArgs<float> &, cudaStream_t);
-template cudaError_t launch_mode_rk<double, true>(int, int, int, const ModeArgs<double> &, cudaStream_t);
+template cudaError_t launch_mode_rk<float, true, false>(int, int, int, const ModeArgs<float> &, cudaStream_t);
+template cudaError_t launch_mode_rk<double, true, false>(int, int, int, const ModeArgs<double> &, cudaStream_t);
 
 }  // namespace tb

@@ -82,7 +82,8 @@ struct ModeTune {
     int ob = 0;      // output rows per register tile
     int waves = 0;   // thread blocks per SM the grid is sized for
     int rank = -1;   // rank-bounded products (1) or not (0); -1: the built-in rule
-    int bt = 0;      // threads per block (32, 64, 128); 0: the built-in rule
+    int bt = 0;      // threads per column slice (32, 64, 128); 0: the built-in rule
+    int sub = 0;     // column slices sharing each column (1, 2, 4); 0: one
 };
 
 struct GraphEntry {
@@ -161,6 +162,7 @@ struct tb_plan {
     int level_choice = 0;          // tb_options.level_schedule
     int core_rows = 1;             // forward complex64 core with one RHS: row batches per warp (k_core_rows)
     int core_mode = 0;             // tb_options.core_mode
+    int mode_slices = 0;           // tb_options.mode_slices
     int core_regen_tuned = 0;      // tb_autotune found the regenerated core faster
     tb::CoreRegen rg{};            // regeneration parameters (rg.kind = 0: not possible)
     int sep_choice = 0;            // separable apply: tb_options.sep_schedule

@@ -43,6 +43,27 @@ def test_version_and_defaults(lib):
     assert lib.tb_options_default(ctypes.byref(opt)) == 0
     assert opt.L == -1 and opt.proxy_rows == 1024 and opt.rank_max == 32 and opt.separable == -1
     assert opt.sep_schedule == 0
+    assert opt.mode_slices == 0
+
+
+def test_build_rejects_an_unknown_slice_count_without_touching_the_gpu(lib):
+    import numpy as np
+    kern = tb._Kernel(tb.KERNEL_FOURIER, (ctypes.c_double * 4)())
+    xs = [np.arange(16) / 16.0 for _ in range(2)]
+    ys = [np.arange(16) - 8.0 for _ in range(2)]
+    grids = tb._Grids()
+    for k in range(2):
+        grids.x[k] = xs[k].ctypes.data
+        grids.y[k] = ys[k].ctypes.data
+    opt = tb._Options()
+    assert lib.tb_options_default(ctypes.byref(opt)) == 0
+    opt.mode_slices = 3
+    n = (ctypes.c_int64 * 2)(16, 16)
+    h = ctypes.c_void_p()
+    assert lib.tb_build_ex(ctypes.byref(kern), 2, ctypes.cast(n, ctypes.c_void_p), ctypes.byref(grids), 1e-6,
+                           ctypes.byref(opt), ctypes.byref(h)) == 1
+    assert b"mode_slices" in lib.tb_last_error()
+    assert not h.value
 
 
 def test_build_rejects_an_unknown_separable_schedule_without_touching_the_gpu(lib):

@@ -2,10 +2,11 @@
 scheduled, never what it computes.
 
 For a non-separable handle it picks, per level pass, side and mode, the
-output rows per register tile and the grid size; every output entry is still
-the same sum over the same fiber in the same order, so the tuned apply must
-equal the untuned one bit for bit (forward and adjoint) within one form of
-the level passes (per-mode launches, or fused launches).  With the built-in
+output rows per register tile, the grid size, the rank bounds, the threads per
+block and the column slices; every output entry is still the same sum over the
+same fiber in the same order (the rank bounds skip only exact zeros), so the
+tuned apply must equal the untuned one bit for bit (forward and adjoint)
+within one form of the level passes (per-mode launches, or fused launches).  With the built-in
 rule it also picks per pass the faster of the two forms, which round
 differently (FP32): there the bar is the complex64 rounding.  For a separable
 handle it picks between per-mode fiber passes and multi-mode tile passes,
@@ -49,6 +50,25 @@ def test_tuned_apply_is_bitwise_the_untuned_apply(name, n, L, nv):
         assert torch.equal(u0, u1)
         assert torch.equal(v0, v1)
     op.close()
+
+
+@pytest.mark.parametrize("name,n,L,nv", [("helmholtz3d_n64", 16, 2, 1), ("helmholtz3d_n64", 32, 2, 3),
+                                         ("radon2d_n256", 64, 4, 1), ("radon2d_n256", 128, 6, 2)])
+def test_column_slices_are_bitwise_the_unsliced_apply(name, n, L, nv):
+    # 2 or 4 groups of threads share each output column (each takes every
+    # 2nd / 4th child or row chunk); complex128 ignores the option
+    w = W.small(name, n, nv=nv, L=L)
+    kw = dict(precisions=(1 << tb.PREC_C64) | (1 << tb.PREC_C128), level_schedule=tb.LEVEL_PER_MODE)
+    ref = tb.from_workload(w, mode_slices=1, **kw)
+    for prec in (tb.PREC_C64, tb.PREC_C128):
+        f = W.rhs(w).to(tb.dtype_of(prec)).cuda()
+        u0, v0 = ref.apply(f, prec).clone(), ref.apply_adjoint(f, prec).clone()
+        for s in (2, 4):
+            op = tb.from_workload(w, mode_slices=s, **kw)
+            assert torch.equal(op.apply(f, prec), u0), (s, prec)
+            assert torch.equal(op.apply_adjoint(f, prec), v0), (s, prec)
+            op.close()
+    ref.close()
 
 
 def test_autotune_option_tunes_at_the_first_apply_and_matches_the_oracle():
