@@ -21,6 +21,13 @@
 // only rows a < rank (and stores zeros past them) or reads only inputs
 // b < rank.  The skipped terms are exact zeros: results do not change.
 //
+// Block shape.  A block has 32, 64 or 128 threads, the fewest that give each
+// column of a unit a thread (units with few columns leave fewer lanes idle).
+// With column slices (SL), S = 2 or 4 groups of threads share each column slot
+// and take every S-th (child, row chunk) item of the column, which spreads a
+// launch with few columns over S times as many warps.  Neither changes what a
+// column computes, nor the order of its sums.
+//
 // Two launches are group-wide.  The first mode of a Split reads the combined
 // parent tile (dims 2 R_{l-1,k}) straight from the 2^d parent tiles and feeds
 // all 2^d children from one fiber; the last mode of a Gather sums the 2^d
