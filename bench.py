@@ -58,6 +58,8 @@ def parse():
                    help="non-separable handles: tb_options.level_schedule (0 rule, 1 per-mode, 2 fused)")
     p.add_argument("--core-mode", type=int, default=0,
                    help="tb_options.core_mode (0 rule, 1 stored cores, 2 regenerated in the one-RHS forward core)")
+    p.add_argument("--mode-slices", type=int, default=0,
+                   help="tb_options.mode_slices (0 rule / tuner; 1, 2, 4 thread groups per column of a mode launch)")
     p.add_argument("--sep-schedule", type=int, default=0,
                    help="separable handles: tb_options.sep_schedule (0 rule; the tuner may replace it)")
     return p.parse_args()
@@ -340,7 +342,7 @@ def main():
     mask = (1 << prec) | ((1 << tb.PREC_C128) if not args.no_fp64 else 0)
     op = tb.from_workload(w, precisions=mask, use_graphs=not args.profile_only, precision=prec,
                           sep_schedule=args.sep_schedule, level_schedule=args.level_schedule,
-                          core_mode=args.core_mode)
+                          core_mode=args.core_mode, mode_slices=args.mode_slices)
     info = op.info()
     nv = w.nv
     tune_s = None
