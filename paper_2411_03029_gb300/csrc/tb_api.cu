@@ -1481,7 +1481,7 @@ tb_status level_pass_fused(const tb_plan *h, Pass pass, bool conj, int side, int
                            int64_t nv, cudaStream_t st, void *scratch, size_t scratch_bytes, bool &done,
                            bool dry = false, int vc_set = 0, int cps_set = 0, int obmax_set = 0) {
     done = false;
-    const int d = h->d, Lc = h->Lc;
+    const int d = h->d;
     if (d > 3 || (1 << d) > level_max_children()) return TB_OK;
     const bool leaf = pass == Pass::LeafIn || pass == Pass::LeafOut;
     LevelArgs a;
@@ -2500,6 +2500,7 @@ tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, cons
                                     for (int bi = 0, bt0 = 0; bi < 2 && status == TB_OK; ++bi)
                                         for (int sb = 1; sb <= 4 && status == TB_OK; sb *= 2) {
                                             if (bi == 1 && bt0 == 128) break;   // the same launches as bi = 0
+                                            if (h->mode_slices && sb != h->mode_slices) continue;   // forced
                                             const int cw = bi == 0 ? bt0 : bts[bi];
                                             if (sb > 1 && (sb * cw > 128 || ri)) break;
                                             float t = 0.f;
@@ -2507,7 +2508,7 @@ tb_status tune_impl(tb_plan *h, int64_t nv, int precision, cudaStream_t st, cons
                                                 [&] {
                                                     return level_pass<R>(h, p, false, side, l, in, out, nv, st, T, k,
                                                                          obs[i], w, 0, -1, rk, bts[bi],
-                                                                         (bi == 0 && sb == 1) ? &bt0 : nullptr, sb);
+                                                                         bi == 0 ? &bt0 : nullptr, sb);
                                                 },
                                                 t);
                                             if (status != TB_OK) break;
