@@ -80,7 +80,7 @@ k_interp_decomp(const IdArgs a) {
     const int tid = threadIdx.x, bd = blockDim.x;
     const int d = a.d, l = a.l, Lc = a.Lc;
 
-    __shared__ int cand[ID_NCMAX], colpos[ID_NCMAX], piv[ID_NCMAX], ipiv[ID_NCMAX];
+    __shared__ int cand[ID_NCMAX], piv[ID_NCMAX], ipiv[ID_NCMAX];
     __shared__ int rsize[2 * MAXD], rstart[2 * MAXD], rmode[2 * MAXD], rside[2 * MAXD];
     __shared__ uint32_t rsalt[2 * MAXD];
     __shared__ int64_t rstride[2 * MAXD];
@@ -128,10 +128,7 @@ k_interp_decomp(const IdArgs a) {
         if (l == 0) {
             const int64_t base = (int64_t)sh_F[k] * (a.n[k] >> Lc) + (int64_t)sg * a.cb[k];
             nc = a.cb[k];
-            for (int c = 0; c < nc; ++c) {
-                cand[c] = a.perm[k][base + c];
-                colpos[c] = c;
-            }
+            for (int c = 0; c < nc; ++c) cand[c] = a.perm[k][base + c];
         } else {
             int64_t jp;
             if (!a.separable) {
@@ -148,8 +145,8 @@ k_interp_decomp(const IdArgs a) {
             const int pc = a.pcap[k];
             r1 = a.prank[k][jp];
             const int r2 = a.prank[k][jp + 1];
-            for (int c = 0; c < r1; ++c) { cand[nc] = ps[jp * pc + c]; colpos[nc] = c; ++nc; }
-            for (int c = 0; c < r2; ++c) { cand[nc] = ps[(jp + 1) * pc + c]; colpos[nc] = a.pR[k] + c; ++nc; }
+            for (int c = 0; c < r1; ++c) cand[nc++] = ps[jp * pc + c];
+            for (int c = 0; c < r2; ++c) cand[nc++] = ps[(jp + 1) * pc + c];
         }
         sh_nc = nc;
         sh_r1 = r1;

@@ -329,7 +329,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1) k_core_tc(const CoreTcArgs a) 
     } else if (warp >= EPI_WARP0) {
         // --------------------------------------------------------- epilogue
         const int q = warp & 3;   // the TMEM lane quarter this warp may read
-        const int et = tid - EPI_WARP0 * 32;
         int64_t ni = 0;
         for (int64_t item = blockIdx.x; item < a.nitems; item += gridDim.x, ++ni) {
             const CoreItem it = a.items[item];

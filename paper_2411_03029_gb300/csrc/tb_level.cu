@@ -32,7 +32,6 @@ namespace tb {
 
 constexpr int LV_THREADS = 256;
 constexpr int LV_MAXCH = 8;   // children of a group (d <= 3)
-constexpr int LV_XB = 6;      // input values of a fiber loaded ahead
 
 namespace {
 
